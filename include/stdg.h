@@ -1,0 +1,158 @@
+/*
+ * stdg.h - C ABI of the GB300 space-time DG-SEM library (libstdg.so).
+ *
+ * Method: the space-time discontinuous Galerkin spectral element method of
+ * Versbach, Linders, Kloefkorn and Birken, "Theoretical and Practical Aspects
+ * of Space-Time DG-SEM Implementations" (arXiv:2201.05800).  One time slab
+ * (one temporal element, Sec. 4) carries s = N_tau temporal LGL nodes; its
+ * nonlinear system is Eq. DG_vs_RK:DG, solved by Jacobian-free Newton-Krylov
+ * (Newton + restarted GMRES, Sec. 6.3 "Nonlinear solvers and preconditioning").
+ *
+ * Problem (Eq. general with F_v = 0, S = 0): d_t u + div F_c(u) = 0 on a
+ * uniform periodic Cartesian grid (Sec. 3.1), with
+ *   STDG_ADVECTION  u_t + a . grad u = 0              (r = 1)
+ *   STDG_EULER      Euler equations, Eqs. eulereq/defu (r = d + 2,
+ *                   u = (rho, rho v_1..rho v_d, E))
+ *   STDG_BURGERS    u_t + div(u^2/2 (1,..,1)) = 0      (r = 1)
+ * and the Rusanov (local Lax-Friedrichs) flux of Eq. flux:llf on every face
+ * (exact upwind for advection).  Initial data are nodal values on the LGL
+ * nodes (interpolation = the quadrature projection of Eq. ode).
+ *
+ * Discrete residual evaluated by the library (the reading that makes its
+ * Jacobian exactly Eq. Jacobian_ST):
+ *   R(U) = (D_tau^T M_tau (x) I) U - (B_tau (x) I) U* + dt/2 (M_tau (x) I) F(U),
+ *   U* = (u_prev, 0, ..., 0, U^s)                        (Eq. upwind_flux),
+ * with F = M^-1 L_h the spatial DG-SEM operator (Eqs. elementint, surfaceint,
+ * ode).  The slab solution is R(U) = 0 and the new state u^{n+1} = U^s (Eq. un).
+ *
+ * Layouts (all arrays dense, FP64, C order):
+ *   element index e = (ez*Ky + ey)*Kx + ex, spatial node (iz, iy, ix) with ix
+ *   fastest, r components fastest of all.
+ *   state (one time level): u[e][iz][iy][ix][c]          stdg_state_len values
+ *   slab  (s time nodes):   U[e][m][iz][iy][ix][c]       stdg_slab_len values
+ *   node coordinates:       X[e][iz][iy][ix][a]          stdg_state_len/r*d values
+ *
+ * Pointers: ptr_kind STDG_HOST means ordinary host memory (copied in and out
+ * on the context's stream, synchronously); STDG_DEVICE means device memory of
+ * the current CUDA device, read and written in stream order on the context's
+ * stream (the call returns once the work is enqueued, except where a value
+ * must come back to the host).  The library never keeps a caller pointer past
+ * the call and never frees caller memory; it owns the device memory inside a
+ * context, freed by stdg_destroy.
+ *
+ * Errors: every call returns a stdg_status; no call throws, exits or traps.
+ * stdg_last_error(ctx) gives a message for the last failing call on ctx.
+ * A context is used by one host thread at a time.
+ */
+#ifndef STDG_H
+#define STDG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stdg_ctx stdg_ctx;
+
+typedef enum {
+  STDG_OK = 0,
+  STDG_ERR_INVALID_ARG = 1,      /* a NULL pointer, a size or option out of range      */
+  STDG_ERR_OOM = 2,              /* device allocation failed or over hbm_budget_bytes  */
+  STDG_ERR_CUDA = 3,             /* a CUDA runtime call failed (message in last_error) */
+  STDG_ERR_NOT_CONVERGED = 4,    /* Newton hit newton_maxit before its tolerance       */
+  STDG_ERR_GMRES_BREAKDOWN = 5,  /* GMRES stagnated at gmres_maxit with no progress    */
+  STDG_ERR_NAN = 6,              /* a residual norm was NaN or Inf                     */
+  STDG_ERR_TIMEOUT = 7,          /* reserved: a bounded device wait ran out            */
+  STDG_ERR_CANCELLED = 8,        /* reserved: request cancelled by the caller          */
+  STDG_ERR_UNSUPPORTED = 9       /* valid but not compiled in (e.g. dim/N combination) */
+} stdg_status;
+
+enum { STDG_ADVECTION = 0, STDG_EULER = 1, STDG_BURGERS = 2 };
+enum { STDG_FLUX_RUSANOV = 0 };             /* Eq. flux:llf; upwind for advection       */
+enum { STDG_FP64 = 0, STDG_MIXED_FP32 = 1 };/* precision of Jv and the GMRES basis       */
+enum { STDG_JV_FD = 0, STDG_JV_EXACT = 1 }; /* finite-difference JFNK or forward mode    */
+enum { STDG_HOST = 0, STDG_DEVICE = 1 };
+
+typedef struct {
+  int dim;                  /* spatial dimension d, 1..3                                 */
+  int cells[3];             /* elements per direction (entries beyond dim ignored), >= 1 */
+  double lo[3], hi[3];      /* periodic box [lo, hi] per direction                       */
+  int N;                    /* spatial degree, n = N+1 LGL nodes per direction, 1..7      */
+  int s;                    /* temporal LGL nodes N_tau (= Lobatto IIIC stages), 2..5    */
+  int equation;             /* STDG_ADVECTION | STDG_EULER | STDG_BURGERS                */
+  double adv_vel[3];        /* advection velocity a                                      */
+  double gamma;             /* ratio of specific heats (Euler)                           */
+  int flux;                 /* STDG_FLUX_RUSANOV                                         */
+  double dt;                /* slab length Delta t_n > 0                                 */
+  int precision;            /* STDG_FP64 | STDG_MIXED_FP32                               */
+  int jv_mode;              /* STDG_JV_FD | STDG_JV_EXACT                                */
+  double newton_rtol;       /* stop when ||R||_2 <= max(rtol ||R(U0)||_2, atol)          */
+  double newton_atol;
+  int newton_maxit;         /* >= 1                                                      */
+  int gmres_m;              /* restart length, 1..64                                     */
+  double gmres_rtol;        /* inner tolerance eta (relative to ||R||)                   */
+  int gmres_maxit;          /* total inner iterations per Newton step, >= 1              */
+  size_t hbm_budget_bytes;  /* 0 = unlimited; else create fails with STDG_ERR_OOM above  */
+} stdg_config_desc;
+
+typedef struct {
+  int newton_its;           /* Newton steps taken                                        */
+  int gmres_its;            /* GMRES iterations summed over the Newton steps             */
+  int residual_evals;       /* FP64 residual evaluations                                 */
+  int jv_evals;             /* Jacobian-vector products                                  */
+  double res0;              /* ||R(U0)||_2 with U0 = 1 (x) u^n                           */
+  double res_final;         /* ||R(U)||_2 at exit                                        */
+} stdg_slab_stats;
+
+/* Fill *desc with defaults (1D advection, N=3, s=3, FP64, FD Jv, GMRES(30)). */
+void stdg_config_default(stdg_config_desc* desc);
+
+/* Create a context on the current CUDA device; cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream) on which all work of the context is ordered.
+ * Allocates every device buffer the slab solve needs (state, slab, residual,
+ * Krylov basis of gmres_m+1 vectors).  *out is NULL on failure. */
+stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ctx** out);
+stdg_status stdg_destroy(stdg_ctx* ctx);
+
+size_t stdg_state_len(const stdg_ctx* ctx);   /* K * n^d * r                              */
+size_t stdg_slab_len(const stdg_ctx* ctx);    /* K * s * n^d * r                          */
+size_t stdg_coord_len(const stdg_ctx* ctx);   /* K * n^d * d                              */
+size_t stdg_device_bytes(const stdg_ctx* ctx);/* device memory owned by the context       */
+
+/* Physical coordinates of every spatial node (LGL nodes mapped to each element). */
+stdg_status stdg_node_coordinates(const stdg_ctx* ctx, double* X, int ptr_kind);
+
+/* Set / get the current state u^n (one time level). */
+stdg_status stdg_set_state(stdg_ctx* ctx, const double* u, int ptr_kind);
+stdg_status stdg_get_state(const stdg_ctx* ctx, double* u, int ptr_kind);
+/* Get the last solved slab U (all s time nodes). */
+stdg_status stdg_get_slab(const stdg_ctx* ctx, double* U, int ptr_kind);
+
+/* Solve the current slab (Newton-Krylov from U0 = 1 (x) u^n) and advance:
+ * u^n <- U^s, t <- t + dt.  stats may be NULL.  Returns STDG_ERR_NOT_CONVERGED
+ * (state still advanced to the last iterate) or STDG_ERR_NAN (state kept). */
+stdg_status stdg_advance_slab(stdg_ctx* ctx, stdg_slab_stats* stats);
+
+/* R = R(U; u_prev) (slab residual above).  U, R: slab_len; u_prev: state_len. */
+stdg_status stdg_residual(stdg_ctx* ctx, const double* U, const double* u_prev, double* R, int ptr_kind);
+
+/* Jv = J(U) v with J = dR/dU (Eq. Jacobian_ST), by the context's jv_mode:
+ * STDG_JV_FD: [R(U + eps v) - R(U)]/eps with the exact linear temporal part,
+ *             eps = sqrt(machine eps) (1 + ||U||_2) / ||v||_2;
+ * STDG_JV_EXACT: forward-mode derivative (exact up to rounding).
+ * u_prev does not enter J; it is accepted for symmetry with stdg_residual. */
+stdg_status stdg_jv(stdg_ctx* ctx, const double* U, const double* u_prev, const double* v, double* Jv, int ptr_kind);
+
+/* ||x||_2 of a device or host vector of slab_len values (FP64 accumulation). */
+stdg_status stdg_slab_norm(stdg_ctx* ctx, const double* x, int ptr_kind, double* out);
+
+const char* stdg_last_error(const stdg_ctx* ctx);
+const char* stdg_status_string(stdg_status st);
+/* Library version string. */
+const char* stdg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STDG_H */

@@ -1,0 +1,212 @@
+// Vector kernels of the Newton-GMRES slab solver (see blas.cuh).
+#include "blas.cuh"
+
+namespace stdg {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-reduce `cnt` accumulators (cnt <= kMaxDots + 1) and store them at out[0..cnt).
+template <int NACC>
+__device__ __forceinline__ void block_store(double (&acc)[NACC], int cnt, double* out) {
+  __shared__ double red[kRedThreads / 32][NACC];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NACC; ++i) {
+    if (i < cnt) {
+      double v = warp_sum(acc[i]);
+      if (lane == 0) red[wid][i] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < cnt) {
+    double v = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[q][threadIdx.x];
+    out[threadIdx.x] = v;
+  }
+}
+
+template <class TV, class TW>
+__global__ void __launch_bounds__(kRedThreads) multidot_kernel(const TV* __restrict__ V, size_t ld, int k,
+                                                               const TW* __restrict__ w, size_t L,
+                                                               double* __restrict__ partials) {
+  double acc[kMaxDots];
+#pragma unroll
+  for (int i = 0; i < kMaxDots; ++i) acc[i] = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < L; idx += stride) {
+    const double wv = (double)w[idx];
+#pragma unroll
+    for (int i = 0; i < kMaxDots; ++i)
+      if (i < k) acc[i] = fma((double)V[(size_t)i * ld + idx], wv, acc[i]);
+  }
+  block_store(acc, k, partials + (size_t)blockIdx.x * kPartialStride);
+}
+
+template <class TV, class TW, bool DOTS, bool NORM>
+__global__ void __launch_bounds__(kRedThreads) update_kernel(TW* __restrict__ w, const TV* __restrict__ V, size_t ld,
+                                                             int k, const double* __restrict__ coef, double sign,
+                                                             size_t L, double* __restrict__ partials) {
+  __shared__ double c[kMaxDots];
+  if (threadIdx.x < kMaxDots) c[threadIdx.x] = threadIdx.x < k ? sign * coef[threadIdx.x] : 0.0;
+  __syncthreads();
+  constexpr int NA = DOTS ? kMaxDots + 1 : 1;
+  double acc[NA];
+#pragma unroll
+  for (int i = 0; i < NA; ++i) acc[i] = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < L; idx += stride) {
+    double v[kMaxDots];
+    double x = (double)w[idx];
+#pragma unroll
+    for (int i = 0; i < kMaxDots; ++i)
+      if (i < k) {
+        v[i] = (double)V[(size_t)i * ld + idx];
+        x = fma(-c[i], v[i], x);
+      }
+    const TW xs = (TW)x;
+    w[idx] = xs;
+    const double xr = (double)xs;
+    if (DOTS) {
+#pragma unroll
+      for (int i = 0; i < kMaxDots; ++i)
+        if (i < k) acc[i] = fma(v[i], xr, acc[i]);
+      acc[NA - 1] = fma(xr, xr, acc[NA - 1]);
+    } else if (NORM) {
+      acc[0] = fma(xr, xr, acc[0]);
+    }
+  }
+  if (DOTS || NORM) {
+    double* out = partials + (size_t)blockIdx.x * kPartialStride;
+    if (DOTS) {
+      // dots at [0, k), norm^2 at k
+      double a2[kMaxDots + 1];
+#pragma unroll
+      for (int i = 0; i < kMaxDots + 1; ++i) a2[i] = (i < k) ? acc[i] : (i == k ? acc[NA - 1] : 0.0);
+      block_store(a2, k + 1, out);
+    } else {
+      double a1[1] = {acc[0]};
+      block_store(a1, 1, out);
+    }
+  }
+}
+
+__global__ void reduce_kernel(const double* __restrict__ partials, int nblk, double* __restrict__ out) {
+  // one block per output index; fixed-order tree
+  __shared__ double sh[kRedThreads];
+  const int i = blockIdx.x;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += partials[(size_t)b * kPartialStride + i];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[i] = sh[0];
+}
+
+template <class TX, class TY>
+__global__ void scale_add_kernel(TY* y, const TX* x, double a, const TX* z, double b, size_t L) {
+  // y may alias x or z (in-place scaling and updates): no __restrict__ here
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < L; idx += stride) {
+    double v = a * (double)x[idx];
+    if (z) v = fma(b, (double)z[idx], v);
+    y[idx] = (TY)v;
+  }
+}
+
+template <class T>
+__global__ void broadcast_kernel(T* __restrict__ U, const T* __restrict__ u, long long nelem, int s, int blk) {
+  const size_t total = (size_t)nelem * s * blk;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+    size_t e = idx / ((size_t)s * blk);
+    size_t q = idx % blk;
+    U[idx] = u[e * blk + q];
+  }
+}
+
+template <class T>
+__global__ void extract_kernel(T* __restrict__ u, const T* __restrict__ U, long long nelem, int s, int blk) {
+  const size_t total = (size_t)nelem * blk;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+    size_t e = idx / blk, q = idx % blk;
+    u[idx] = U[(e * s + (s - 1)) * blk + q];
+  }
+}
+
+unsigned grid_for(size_t L) {
+  size_t b = (L + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+template <class TV, class TW>
+cudaError_t multidot(const TV* V, size_t ld, int k, const TW* w, size_t L, double* partials, int nblk,
+                     cudaStream_t st) {
+  if (k < 1 || k > kMaxDots) return cudaErrorInvalidValue;
+  multidot_kernel<TV, TW><<<nblk, kRedThreads, 0, st>>>(V, ld, k, w, L, partials);
+  return cudaGetLastError();
+}
+
+template <class TV, class TW>
+cudaError_t update(TW* w, const TV* V, size_t ld, int k, const double* coef, double coef_sign, size_t L,
+                   double* partials, int nblk, bool dots, bool norm, cudaStream_t st) {
+  if (k < 0 || k > kMaxDots) return cudaErrorInvalidValue;
+  if (dots)
+    update_kernel<TV, TW, true, true><<<nblk, kRedThreads, 0, st>>>(w, V, ld, k, coef, coef_sign, L, partials);
+  else if (norm)
+    update_kernel<TV, TW, false, true><<<nblk, kRedThreads, 0, st>>>(w, V, ld, k, coef, coef_sign, L, partials);
+  else
+    update_kernel<TV, TW, false, false><<<nblk, kRedThreads, 0, st>>>(w, V, ld, k, coef, coef_sign, L, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t reduce_partials(const double* partials, int nblk, int count, double* out, cudaStream_t st) {
+  if (count < 1) return cudaSuccess;
+  reduce_kernel<<<count, kRedThreads, 0, st>>>(partials, nblk, out);
+  return cudaGetLastError();
+}
+
+template <class TX, class TY>
+cudaError_t scale_add(TY* y, const TX* x, double a, const TX* z, double b, size_t L, cudaStream_t st) {
+  scale_add_kernel<TX, TY><<<grid_for(L), 256, 0, st>>>(y, x, a, z, b, L);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t broadcast_slab(T* U, const T* u, long long nelem, int s, int blk, cudaStream_t st) {
+  broadcast_kernel<T><<<grid_for((size_t)nelem * s * blk), 256, 0, st>>>(U, u, nelem, s, blk);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t extract_last(T* u, const T* U, long long nelem, int s, int blk, cudaStream_t st) {
+  extract_kernel<T><<<grid_for((size_t)nelem * blk), 256, 0, st>>>(u, U, nelem, s, blk);
+  return cudaGetLastError();
+}
+
+template cudaError_t multidot<double, double>(const double*, size_t, int, const double*, size_t, double*, int, cudaStream_t);
+template cudaError_t multidot<float, float>(const float*, size_t, int, const float*, size_t, double*, int, cudaStream_t);
+template cudaError_t update<double, double>(double*, const double*, size_t, int, const double*, double, size_t, double*, int, bool, bool, cudaStream_t);
+template cudaError_t update<float, float>(float*, const float*, size_t, int, const double*, double, size_t, double*, int, bool, bool, cudaStream_t);
+template cudaError_t update<float, double>(double*, const float*, size_t, int, const double*, double, size_t, double*, int, bool, bool, cudaStream_t);
+template cudaError_t scale_add<double, double>(double*, const double*, double, const double*, double, size_t, cudaStream_t);
+template cudaError_t scale_add<double, float>(float*, const double*, double, const double*, double, size_t, cudaStream_t);
+template cudaError_t scale_add<float, float>(float*, const float*, double, const float*, double, size_t, cudaStream_t);
+template cudaError_t scale_add<float, double>(double*, const float*, double, const float*, double, size_t, cudaStream_t);
+template cudaError_t broadcast_slab<double>(double*, const double*, long long, int, int, cudaStream_t);
+template cudaError_t extract_last<double>(double*, const double*, long long, int, int, cudaStream_t);
+
+}  // namespace stdg

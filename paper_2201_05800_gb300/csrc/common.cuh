@@ -1,0 +1,167 @@
+// Device-side building blocks of the space-time DG-SEM operator: kernel
+// arguments, dual numbers (forward-mode derivatives for the exact Jacobian-
+// vector product) and the convective physics with the Rusanov flux.
+//
+// Physics (arXiv:2201.05800):
+//   Euler equations, Eqs. eulereq/defu and the flux f_i printed after them
+//   (Sec. 7.3); linear advection f_i = a_i u; Burgers f_i = u^2/2.
+//   Rusanov flux, Eq. flux:llf, on a face with normal +e_a between a left state
+//   uL and a right state uR:  H = (f_a(uL) + f_a(uR))/2 - lambda/2 (uR - uL),
+//   lambda = max(|v_a| + c) over the two states (ties take the left state).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "stdg.h"
+
+namespace stdg {
+
+constexpr int kMaxN = 8;  // LGL nodes per direction (spatial degree N <= 7)
+constexpr int kMaxS = 5;  // temporal LGL nodes N_tau
+
+// Operator modes.
+enum OpMode {
+  kModeResidual = 0,  // out = R(U; u_prev) (if out), fout = F(U) (if fout)
+  kModeJvFD = 1,      // out = J(U) v by a one-sided difference of F around F0 = F(U)
+  kModeJvExact = 2    // out = J(U) v by forward-mode (dual-number) differentiation
+};
+
+// Arguments of one operator launch.  Constants are already scaled for the
+// strong form: F_I = -sum_a ginv_a [ (D f_a)_I + winv_end (face corrections) ].
+template <class T>
+struct OpArgs {
+  int n, s, nd, epb;       // LGL nodes per direction, temporal nodes, n^d, elements per block
+  int K[3];                // elements per direction
+  long long nelem;
+  T D[kMaxN][kMaxN];       // D[i][j] = l_j'(xi_i) on [-1, 1]
+  T C[kMaxS][kMaxS];       // C[j][m] = omega_j Dtau[j][m], i.e. (D_tau^T M_tau)[m][j]
+  T omega[kMaxS];          // temporal LGL weights
+  T ginv[3];               // 2 / h_a
+  T winv_end;              // 1 / w_0 = 1 / w_N (end weights of the spatial LGL rule)
+  T half_dt;               // Delta t / 2
+  T gamma;
+  T adv[3];
+  T eps;                   // FD step (kModeJvFD)
+  T vscale;                // v is read as vscale * v (kModeJvFD / kModeJvExact)
+  const T* U;              // slab, [e][m][node][c]
+  const T* v;              // direction, same layout
+  const T* F0;             // F(U), same layout (kModeJvFD)
+  const T* uprev;          // previous slab trace, [e][node][c] (kModeResidual)
+  T* out;                  // R or Jv (may be null in kModeResidual)
+  T* fout;                 // F(U) (kModeResidual, may be null)
+};
+
+// ---------------------------------------------------------------- dual numbers
+template <class T>
+struct Dual {
+  T v, d;
+};
+
+template <class T> __device__ __forceinline__ T val(T x) { return x; }
+template <class T> __device__ __forceinline__ T val(Dual<T> x) { return x.v; }
+
+template <class T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, Dual<T> b) { return {a.v + b.v, a.d + b.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return {a.v - b.v, a.d - b.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a) { return {-a.v, -a.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) { return {a.v * b.v, a.v * b.d + a.d * b.v}; }
+template <class T> __device__ __forceinline__ Dual<T> operator*(T a, Dual<T> b) { return {a * b.v, a * b.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, T b) { return {a.v * b, a.d * b}; }
+template <class T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, T b) { return {a.v + b, a.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, T b) { return {a.v - b, a.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator-(T a, Dual<T> b) { return {a - b.v, -b.d}; }
+template <class T> __device__ __forceinline__ Dual<T> recip(Dual<T> a) {
+  T r = T(1) / a.v;
+  return {r, -a.d * r * r};
+}
+template <class T> __device__ __forceinline__ T recip(T a) { return T(1) / a; }
+template <class T> __device__ __forceinline__ Dual<T> dsqrt(Dual<T> a) {
+  T r = sqrt(a.v);
+  return {r, a.d * (T(0.5) / r)};
+}
+template <class T> __device__ __forceinline__ T dsqrt(T a) { return sqrt(a); }
+template <class T> __device__ __forceinline__ Dual<T> dabs(Dual<T> a) { return a.v >= T(0) ? a : -a; }
+template <class T> __device__ __forceinline__ T dabs(T a) { return fabs(a); }
+// max with the branch chosen on the values; ties take the first argument
+template <class V> __device__ __forceinline__ V dmax(V a, V b) { return val(a) >= val(b) ? a : b; }
+
+template <class V, class T> struct Lift { __device__ static V from(T x) { return x; } };
+template <class T> struct Lift<Dual<T>, T> { __device__ static Dual<T> from(T x) { return {x, T(0)}; } };
+
+// ---------------------------------------------------------------- physics
+template <int EQ, int DIM> struct Phys;
+
+template <int DIM>
+struct Phys<STDG_ADVECTION, DIM> {
+  static constexpr int R = 1;
+  template <class V, class T>
+  __device__ static void flux_all(const V* u, V (*f)[R], const OpArgs<T>& k) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) f[a][0] = k.adv[a] * u[0];
+  }
+  template <class V, class T>
+  __device__ static void flux(const V* u, int a, V* f, const OpArgs<T>& k) { f[0] = k.adv[a] * u[0]; }
+  template <class V, class T>
+  __device__ static V speed(const V* u, int a, const OpArgs<T>& k) { return Lift<V, T>::from(fabs(k.adv[a])); }
+};
+
+template <int DIM>
+struct Phys<STDG_BURGERS, DIM> {
+  static constexpr int R = 1;
+  template <class V, class T>
+  __device__ static void flux_all(const V* u, V (*f)[R], const OpArgs<T>& k) {
+    V h = T(0.5) * (u[0] * u[0]);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) f[a][0] = h;
+  }
+  template <class V, class T>
+  __device__ static void flux(const V* u, int a, V* f, const OpArgs<T>& k) { f[0] = T(0.5) * (u[0] * u[0]); }
+  template <class V, class T>
+  __device__ static V speed(const V* u, int a, const OpArgs<T>& k) { return dabs(u[0]); }
+};
+
+template <int DIM>
+struct Phys<STDG_EULER, DIM> {
+  static constexpr int R = DIM + 2;
+  // pressure p = (gamma - 1) (E - |m|^2 / (2 rho)) given 1/rho
+  template <class V, class T>
+  __device__ static V pressure(const V* u, V irho, const OpArgs<T>& k) {
+    V m2 = u[1] * u[1];
+#pragma unroll
+    for (int b = 1; b < DIM; ++b) m2 = m2 + u[1 + b] * u[1 + b];
+    return (k.gamma - T(1)) * (u[R - 1] - T(0.5) * (m2 * irho));
+  }
+  template <class V, class T>
+  __device__ static void flux_all(const V* u, V (*f)[R], const OpArgs<T>& k) {
+    V irho = recip(u[0]);
+    V p = pressure(u, irho, k);
+    V Ep = u[R - 1] + p;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      V va = u[1 + a] * irho;
+      f[a][0] = u[1 + a];
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) f[a][1 + b] = (b == a) ? u[1 + b] * va + p : u[1 + b] * va;
+      f[a][R - 1] = Ep * va;
+    }
+  }
+  template <class V, class T>
+  __device__ static void flux(const V* u, int a, V* f, const OpArgs<T>& k) {
+    V irho = recip(u[0]);
+    V p = pressure(u, irho, k);
+    V va = u[1 + a] * irho;
+    f[0] = u[1 + a];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) f[1 + b] = (b == a) ? u[1 + b] * va + p : u[1 + b] * va;
+    f[R - 1] = (u[R - 1] + p) * va;
+  }
+  // |v_a| + sqrt(gamma p / rho)
+  template <class V, class T>
+  __device__ static V speed(const V* u, int a, const OpArgs<T>& k) {
+    V irho = recip(u[0]);
+    V p = pressure(u, irho, k);
+    return dabs(u[1 + a] * irho) + dsqrt(k.gamma * (p * irho));
+  }
+};
+
+}  // namespace stdg

@@ -1,0 +1,600 @@
+// C-ABI of libstdg: context, residual / Jv entry points and the Newton-Krylov
+// slab solver (see include/stdg.h for the contract).
+//
+// Slab solve (Sec. 6.3, Newton-type nonlinear solver with a Krylov linear
+// solver, as in the paper's 3D runs): U0 = 1 (x) u^n; while ||R(U)|| is above
+// max(rtol ||R(U0)||, atol): solve J(U) dU = -R(U) by restarted GMRES(m) with
+// classical Gram-Schmidt and one re-orthogonalisation pass (CGS2), Givens
+// rotations on the host, matrix-free J v by the space-time operator kernel;
+// U += dU.  Then u^{n+1} = U^s (Eq. un).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "blas.cuh"
+#include "common.cuh"
+#include "lgl_host.h"
+#include "ops.h"
+#include "stdg.h"
+
+using namespace stdg;
+
+namespace {
+
+constexpr int kMaxGmresM = kMaxDots - 1;  // basis of m+1 vectors must fit one dot pass
+constexpr size_t kSmemLimit = 227 * 1024;
+constexpr int kSmall = 256;               // doubles of device / pinned scratch
+
+}  // namespace
+
+struct stdg_ctx {
+  stdg_config_desc d;
+  cudaStream_t st = nullptr;
+  int device = 0, sms = 0;
+  int dim = 1, n = 2, s = 2, r = 1, nd = 1;
+  long long nelem = 0;
+  size_t state_len = 0, slab_len = 0;
+  double h[3] = {1, 1, 1};
+  OpArgs<double> a64;
+  OpArgs<float> a32;
+  int epb64[3] = {1, 1, 1};
+  int nblk = 1;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  double *U = nullptr, *R = nullptr, *F0 = nullptr, *delta = nullptr, *uprev = nullptr;
+  double *X1 = nullptr, *X2 = nullptr, *Xs = nullptr, *V = nullptr, *partials = nullptr, *small = nullptr;
+  double* hpin = nullptr;
+  double t = 0.0;
+  bool have_slab = false;
+  std::string err;
+};
+
+namespace {
+
+struct DevGuard {
+  int prev = -1, dev;
+  explicit DevGuard(int d) : dev(d) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DevGuard() {
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+  }
+};
+
+stdg_status fail(stdg_ctx* c, stdg_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+#define CK(c, expr)                                                                                   \
+  do {                                                                                                \
+    cudaError_t _e = (expr);                                                                          \
+    if (_e != cudaSuccess)                                                                            \
+      return fail((c), STDG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));            \
+  } while (0)
+
+#define CKS(expr)                        \
+  do {                                   \
+    stdg_status _s = (expr);             \
+    if (_s != STDG_OK) return _s;        \
+  } while (0)
+
+int num_components(int eq, int dim) { return eq == STDG_EULER ? dim + 2 : 1; }
+
+template <class T>
+void fill_args(const stdg_ctx* c, OpArgs<T>& k) {
+  std::memset(&k, 0, sizeof(k));
+  k.n = c->n;
+  k.s = c->s;
+  k.nd = c->nd;
+  k.K[0] = c->d.cells[0];
+  k.K[1] = c->dim > 1 ? c->d.cells[1] : 1;
+  k.K[2] = c->dim > 2 ? c->d.cells[2] : 1;
+  k.nelem = c->nelem;
+  double xi[16], w[16], D[256];
+  lgl_rule(c->n, xi, w);
+  diff_matrix(c->n, xi, D);
+  for (int i = 0; i < c->n; ++i)
+    for (int j = 0; j < c->n; ++j) k.D[i][j] = (T)D[i * c->n + j];
+  double tau[16], om[16], Dt[256];
+  lgl_rule(c->s, tau, om);
+  diff_matrix(c->s, tau, Dt);
+  // (D_tau^T M_tau)[m][j] = Dtau[j][m] omega_j  with Dtau[j][m] = l_m'(tau_j)
+  for (int j = 0; j < c->s; ++j)
+    for (int m = 0; m < c->s; ++m) k.C[j][m] = (T)(om[j] * Dt[j * c->s + m]);
+  for (int m = 0; m < c->s; ++m) k.omega[m] = (T)om[m];
+  for (int a = 0; a < 3; ++a) k.ginv[a] = (T)(a < c->dim ? 2.0 / c->h[a] : 0.0);
+  k.winv_end = (T)(1.0 / w[0]);
+  k.half_dt = (T)(0.5 * c->d.dt);
+  k.gamma = (T)c->d.gamma;
+  for (int a = 0; a < 3; ++a) k.adv[a] = (T)c->d.adv_vel[a];
+  k.vscale = (T)1;
+}
+
+stdg_status validate(const stdg_config_desc* d, std::string* why) {
+  auto bad = [&](const char* m) { *why = m; return STDG_ERR_INVALID_ARG; };
+  if (d->dim < 1 || d->dim > 3) return bad("dim must be 1..3");
+  for (int a = 0; a < d->dim; ++a) {
+    if (d->cells[a] < 1) return bad("cells must be >= 1");
+    if (!(d->hi[a] > d->lo[a])) return bad("hi must exceed lo");
+  }
+  if (d->N < 1 || d->N > 7) return bad("N must be 1..7");
+  if (d->s < 2 || d->s > 5) return bad("s must be 2..5");
+  if (d->equation != STDG_ADVECTION && d->equation != STDG_EULER && d->equation != STDG_BURGERS)
+    return bad("unknown equation");
+  if (d->equation == STDG_BURGERS && d->dim > 2) return bad("Burgers is compiled for dim 1..2");
+  if (d->flux != STDG_FLUX_RUSANOV) return bad("unknown flux");
+  if (!(d->dt > 0) || !std::isfinite(d->dt)) return bad("dt must be positive");
+  if (d->equation == STDG_EULER && !(d->gamma > 1.0)) return bad("gamma must exceed 1");
+  if (d->precision != STDG_FP64 && d->precision != STDG_MIXED_FP32) return bad("unknown precision");
+  if (d->jv_mode != STDG_JV_FD && d->jv_mode != STDG_JV_EXACT) return bad("unknown jv_mode");
+  if (d->newton_maxit < 1 || d->gmres_maxit < 1) return bad("maxit must be >= 1");
+  if (d->gmres_m < 1 || d->gmres_m > kMaxGmresM) return bad("gmres_m must be 1..31");
+  if (!(d->newton_rtol >= 0) || !(d->newton_atol >= 0) || !(d->gmres_rtol > 0)) return bad("bad tolerance");
+  return STDG_OK;
+}
+
+stdg_status alloc(stdg_ctx* c, double** p, size_t count) {
+  size_t b = count * sizeof(double);
+  if (c->d.hbm_budget_bytes && c->bytes + b > c->d.hbm_budget_bytes)
+    return fail(c, STDG_ERR_OOM, "allocation exceeds hbm_budget_bytes");
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, b);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, STDG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(q);
+  c->bytes += b;
+  *p = static_cast<double*>(q);
+  return STDG_OK;
+}
+
+int choose_epb(const stdg_ctx* c, int mode, size_t tsize) {
+  int epb = 256 / c->nd;
+  if (epb < 1) epb = 1;
+  // keep at least ~2 CTAs per SM when the grid allows it
+  long long want = (c->nelem + 2LL * c->sms - 1) / (2LL * c->sms);
+  if (want < 1) want = 1;
+  if (epb > want) epb = (int)want;
+  while (epb > 1 && operator_smem_bytes(c->dim, c->r, tsize, mode, c->n, c->s, epb) > kSmemLimit) --epb;
+  return epb;
+}
+
+// ---- operator launches (FP64)
+stdg_status op_residual(stdg_ctx* c, const double* U, const double* uprev, double* out, double* fout) {
+  OpArgs<double> k = c->a64;
+  k.epb = c->epb64[kModeResidual];
+  k.U = U;
+  k.uprev = uprev;
+  k.out = out;
+  k.fout = fout;
+  CK(c, launch_operator<double>(c->dim, c->d.equation, kModeResidual, k, c->st));
+  return STDG_OK;
+}
+
+stdg_status op_jv(stdg_ctx* c, const double* U, const double* F0, const double* v, double vscale, double eps,
+                  double* out) {
+  const int mode = c->d.jv_mode == STDG_JV_EXACT ? kModeJvExact : kModeJvFD;
+  OpArgs<double> k = c->a64;
+  k.epb = c->epb64[mode];
+  k.U = U;
+  k.v = v;
+  k.F0 = F0;
+  k.vscale = vscale;
+  k.eps = eps;
+  k.out = out;
+  CK(c, launch_operator<double>(c->dim, c->d.equation, mode, k, c->st));
+  return STDG_OK;
+}
+
+// ---- reductions
+stdg_status dots_to_small(stdg_ctx* c, const double* V, int k, const double* w, int small_off) {
+  CK(c, (multidot<double, double>(V, c->slab_len, k, w, c->slab_len, c->partials, c->nblk, c->st)));
+  CK(c, reduce_partials(c->partials, c->nblk, k, c->small + small_off, c->st));
+  return STDG_OK;
+}
+
+stdg_status fetch_small(stdg_ctx* c, int off, int count) {
+  CK(c, cudaMemcpyAsync(c->hpin + off, c->small + off, count * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  return STDG_OK;
+}
+
+stdg_status norm2(stdg_ctx* c, const double* x, size_t L, double* out) {
+  CK(c, (multidot<double, double>(x, L, 1, x, L, c->partials, c->nblk, c->st)));
+  CK(c, reduce_partials(c->partials, c->nblk, 1, c->small + 200, c->st));
+  CKS(fetch_small(c, 200, 1));
+  *out = std::sqrt(c->hpin[200]);
+  return STDG_OK;
+}
+
+double fd_base_eps() { return std::sqrt(2.220446049250313e-16); }
+
+// ---- GMRES(m) for J(U) delta = -R, delta accumulated in c->delta.
+stdg_status gmres(stdg_ctx* c, double beta0, double eps_u, int* its_out, int* jv_out) {
+  const int m = c->d.gmres_m;
+  const size_t L = c->slab_len;
+  const double tol = c->d.gmres_rtol * beta0;
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
+  auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  auto Vrow = [&](int i) { return c->V + (size_t)i * L; };
+  CK(c, cudaMemsetAsync(c->delta, 0, L * sizeof(double), c->st));
+  int its = 0, jvs = 0;
+  bool first = true;
+  while (its < c->d.gmres_maxit) {
+    double beta;
+    if (first) {
+      CK(c, (scale_add<double, double>(Vrow(0), c->R, -1.0 / beta0, nullptr, 0.0, L, c->st)));
+      beta = beta0;
+    } else {
+      double nd;
+      CKS(norm2(c, c->delta, L, &nd));
+      CKS(op_jv(c, c->U, c->F0, c->delta, 1.0, eps_u / (nd > 0 ? nd : 1.0), Vrow(0)));
+      ++jvs;
+      CK(c, (scale_add<double, double>(Vrow(0), c->R, -1.0, Vrow(0), -1.0, L, c->st)));
+      CKS(norm2(c, Vrow(0), L, &beta));
+      if (!(beta > tol)) break;
+      CK(c, (scale_add<double, double>(Vrow(0), Vrow(0), 1.0 / beta, nullptr, 0.0, L, c->st)));
+    }
+    first = false;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int kdim = 0;
+    bool done = false;
+    for (int j = 0; j < m && its < c->d.gmres_maxit; ++j) {
+      double* w = Vrow(j + 1);
+      CKS(op_jv(c, c->U, c->F0, Vrow(j), 1.0, eps_u, w));
+      ++jvs;
+      // CGS2: h1 = V^T w; w -= V h1 (and h2 = V^T w); w -= V h2 (and |w|^2)
+      CKS(dots_to_small(c, c->V, j + 1, w, 0));
+      CK(c, (update<double, double>(w, c->V, L, j + 1, c->small, 1.0, L, c->partials, c->nblk, true, true, c->st)));
+      CK(c, reduce_partials(c->partials, c->nblk, j + 1, c->small + 64, c->st));
+      CK(c, (update<double, double>(w, c->V, L, j + 1, c->small + 64, 1.0, L, c->partials, c->nblk, false, true,
+                                    c->st)));
+      CK(c, reduce_partials(c->partials, c->nblk, 1, c->small + 128, c->st));
+      CK(c, cudaMemcpyAsync(c->hpin, c->small, 129 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(c, cudaStreamSynchronize(c->st));
+      for (int i = 0; i <= j; ++i) Hij(i, j) = c->hpin[i] + c->hpin[64 + i];
+      double hn = std::sqrt(c->hpin[128]);
+      if (!std::isfinite(hn)) return fail(c, STDG_ERR_NAN, "GMRES: non-finite Krylov vector norm");
+      // apply the previous rotations to the new column, then a new one
+      for (int i = 0; i < j; ++i) {
+        double t0 = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+        Hij(i, j) = t0;
+      }
+      double den = std::hypot(Hij(j, j), hn);
+      if (den == 0.0) den = 1e-300;
+      cs[j] = Hij(j, j) / den;
+      sn[j] = hn / den;
+      Hij(j, j) = den;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++its;
+      kdim = j + 1;
+      if (hn > 0.0) CK(c, (scale_add<double, double>(w, w, 1.0 / hn, nullptr, 0.0, L, c->st)));
+      if (std::fabs(g[j + 1]) <= tol || hn <= 1e-300 * beta0) {
+        done = true;
+        break;
+      }
+    }
+    // y = H^-1 g (upper triangular), delta += V y
+    for (int i = kdim - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int q = i + 1; q < kdim; ++q) acc -= Hij(i, q) * y[q];
+      y[i] = acc / Hij(i, i);
+    }
+    if (kdim > 0) {
+      for (int i = 0; i < kdim; ++i) c->hpin[160 + i] = y[i];
+      CK(c, cudaMemcpyAsync(c->small + 160, c->hpin + 160, kdim * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      CK(c, (update<double, double>(c->delta, c->V, L, kdim, c->small + 160, -1.0, L, c->partials, c->nblk, false,
+                                    false, c->st)));
+      // the pinned y must not be overwritten before the copy has run
+      CK(c, cudaStreamSynchronize(c->st));
+    }
+    if (done) break;
+  }
+  *its_out = its;
+  *jv_out = jvs;
+  return STDG_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void stdg_config_default(stdg_config_desc* d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->dim = 1;
+  d->cells[0] = d->cells[1] = d->cells[2] = 16;
+  for (int a = 0; a < 3; ++a) {
+    d->lo[a] = 0.0;
+    d->hi[a] = 1.0;
+  }
+  d->N = 3;
+  d->s = 3;
+  d->equation = STDG_ADVECTION;
+  d->adv_vel[0] = 1.0;
+  d->gamma = 1.4;
+  d->flux = STDG_FLUX_RUSANOV;
+  d->dt = 0.01;
+  d->precision = STDG_FP64;
+  d->jv_mode = STDG_JV_FD;
+  d->newton_rtol = 1e-10;
+  d->newton_atol = 0.0;
+  d->newton_maxit = 20;
+  d->gmres_m = 30;
+  d->gmres_rtol = 1e-3;
+  d->gmres_maxit = 300;
+  d->hbm_budget_bytes = 0;
+}
+
+stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ctx** out) {
+  if (!out) return STDG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc) return STDG_ERR_INVALID_ARG;
+  std::string why;
+  if (validate(desc, &why) != STDG_OK) return STDG_ERR_INVALID_ARG;
+  if (desc->precision == STDG_MIXED_FP32) return STDG_ERR_UNSUPPORTED;
+  stdg_ctx* c = new stdg_ctx();
+  c->d = *desc;
+  c->st = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return STDG_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (c->sms <= 0) c->sms = 1;
+  c->dim = desc->dim;
+  c->n = desc->N + 1;
+  c->s = desc->s;
+  c->r = num_components(desc->equation, desc->dim);
+  c->nd = 1;
+  c->nelem = 1;
+  for (int a = 0; a < c->dim; ++a) {
+    c->nd *= c->n;
+    c->nelem *= desc->cells[a];
+    c->h[a] = (desc->hi[a] - desc->lo[a]) / desc->cells[a];
+  }
+  c->state_len = (size_t)c->nelem * c->nd * c->r;
+  c->slab_len = c->state_len * c->s;
+  fill_args(c, c->a64);
+  fill_args(c, c->a32);
+  for (int mode = 0; mode < 3; ++mode) {
+    c->epb64[mode] = choose_epb(c, mode, sizeof(double));
+    if (operator_smem_bytes(c->dim, c->r, sizeof(double), mode, c->n, c->s, c->epb64[mode]) > kSmemLimit) {
+      delete c;
+      return STDG_ERR_UNSUPPORTED;
+    }
+  }
+  c->nblk = 4 * c->sms;
+  const size_t L = c->slab_len, S = c->state_len;
+  stdg_status st = STDG_OK;
+  if ((st = alloc(c, &c->U, L)) || (st = alloc(c, &c->R, L)) || (st = alloc(c, &c->F0, L)) ||
+      (st = alloc(c, &c->delta, L)) || (st = alloc(c, &c->X1, L)) || (st = alloc(c, &c->X2, L)) ||
+      (st = alloc(c, &c->uprev, S)) || (st = alloc(c, &c->Xs, S)) ||
+      (st = alloc(c, &c->V, L * (size_t)(desc->gmres_m + 1))) ||
+      (st = alloc(c, &c->partials, (size_t)c->nblk * kPartialStride)) || (st = alloc(c, &c->small, kSmall))) {
+    stdg_destroy(c);
+    return st;
+  }
+  if (cudaMallocHost(&c->hpin, kSmall * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    c->hpin = nullptr;
+    stdg_destroy(c);
+    return STDG_ERR_OOM;
+  }
+  if (cudaMemsetAsync(c->uprev, 0, S * sizeof(double), c->st) != cudaSuccess ||
+      cudaMemsetAsync(c->U, 0, L * sizeof(double), c->st) != cudaSuccess ||
+      cudaStreamSynchronize(c->st) != cudaSuccess) {
+    cudaGetLastError();
+    stdg_destroy(c);
+    return STDG_ERR_CUDA;
+  }
+  *out = c;
+  return STDG_OK;
+}
+
+stdg_status stdg_destroy(stdg_ctx* c) {
+  if (!c) return STDG_ERR_INVALID_ARG;
+  DevGuard g(c->device);
+  cudaStreamSynchronize(c->st);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->hpin) cudaFreeHost(c->hpin);
+  cudaGetLastError();
+  delete c;
+  return STDG_OK;
+}
+
+size_t stdg_state_len(const stdg_ctx* c) { return c ? c->state_len : 0; }
+size_t stdg_slab_len(const stdg_ctx* c) { return c ? c->slab_len : 0; }
+size_t stdg_coord_len(const stdg_ctx* c) { return c ? (size_t)c->nelem * c->nd * c->dim : 0; }
+size_t stdg_device_bytes(const stdg_ctx* c) { return c ? c->bytes : 0; }
+
+stdg_status stdg_node_coordinates(const stdg_ctx* cc, double* X, int kind) {
+  stdg_ctx* c = const_cast<stdg_ctx*>(cc);
+  if (!c || !X || (kind != STDG_HOST && kind != STDG_DEVICE)) return STDG_ERR_INVALID_ARG;
+  DevGuard g(c->device);
+  double xi[16], w[16];
+  lgl_rule(c->n, xi, w);
+  std::vector<double> h((size_t)c->nelem * c->nd * c->dim);
+  const int K0 = c->d.cells[0], K1 = c->dim > 1 ? c->d.cells[1] : 1;
+  for (long long e = 0; e < c->nelem; ++e) {
+    long long ec[3] = {e % K0, (e / K0) % K1, e / ((long long)K0 * K1)};
+    for (int node = 0; node < c->nd; ++node) {
+      int idx[3] = {node % c->n, (node / c->n) % c->n, node / (c->n * c->n)};
+      for (int a = 0; a < c->dim; ++a)
+        h[((size_t)e * c->nd + node) * c->dim + a] =
+            c->d.lo[a] + c->h[a] * ((double)ec[a] + 0.5 * (1.0 + xi[idx[a]]));
+    }
+  }
+  if (kind == STDG_HOST) {
+    std::memcpy(X, h.data(), h.size() * sizeof(double));
+  } else {
+    CK(c, cudaMemcpyAsync(X, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+  }
+  return STDG_OK;
+}
+
+stdg_status stdg_set_state(stdg_ctx* c, const double* u, int kind) {
+  if (!c || !u || (kind != STDG_HOST && kind != STDG_DEVICE)) return STDG_ERR_INVALID_ARG;
+  DevGuard g(c->device);
+  CK(c, cudaMemcpyAsync(c->uprev, u, c->state_len * sizeof(double),
+                        kind == STDG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->st));
+  if (kind == STDG_HOST) CK(c, cudaStreamSynchronize(c->st));
+  c->have_slab = false;
+  return STDG_OK;
+}
+
+stdg_status stdg_get_state(const stdg_ctx* cc, double* u, int kind) {
+  stdg_ctx* c = const_cast<stdg_ctx*>(cc);
+  if (!c || !u || (kind != STDG_HOST && kind != STDG_DEVICE)) return STDG_ERR_INVALID_ARG;
+  DevGuard g(c->device);
+  CK(c, cudaMemcpyAsync(u, c->uprev, c->state_len * sizeof(double),
+                        kind == STDG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->st));
+  if (kind == STDG_HOST) CK(c, cudaStreamSynchronize(c->st));
+  return STDG_OK;
+}
+
+stdg_status stdg_get_slab(const stdg_ctx* cc, double* U, int kind) {
+  stdg_ctx* c = const_cast<stdg_ctx*>(cc);
+  if (!c || !U || (kind != STDG_HOST && kind != STDG_DEVICE)) return STDG_ERR_INVALID_ARG;
+  if (!c->have_slab) return fail(c, STDG_ERR_INVALID_ARG, "no slab has been solved since the last set_state");
+  DevGuard g(c->device);
+  CK(c, cudaMemcpyAsync(U, c->U, c->slab_len * sizeof(double),
+                        kind == STDG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->st));
+  if (kind == STDG_HOST) CK(c, cudaStreamSynchronize(c->st));
+  return STDG_OK;
+}
+
+stdg_status stdg_residual(stdg_ctx* c, const double* U, const double* uprev, double* R, int kind) {
+  if (!c || !U || !uprev || !R || (kind != STDG_HOST && kind != STDG_DEVICE)) return STDG_ERR_INVALID_ARG;
+  DevGuard g(c->device);
+  if (kind == STDG_DEVICE) return op_residual(c, U, uprev, R, nullptr);
+  CK(c, cudaMemcpyAsync(c->X1, U, c->slab_len * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CK(c, cudaMemcpyAsync(c->Xs, uprev, c->state_len * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CKS(op_residual(c, c->X1, c->Xs, c->X2, nullptr));
+  CK(c, cudaMemcpyAsync(R, c->X2, c->slab_len * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  return STDG_OK;
+}
+
+stdg_status stdg_jv(stdg_ctx* c, const double* U, const double* uprev, const double* v, double* Jv, int kind) {
+  (void)uprev;
+  if (!c || !U || !v || !Jv || (kind != STDG_HOST && kind != STDG_DEVICE)) return STDG_ERR_INVALID_ARG;
+  DevGuard g(c->device);
+  const double* dU = U;
+  const double* dv = v;
+  double* dout = Jv;
+  if (kind == STDG_HOST) {
+    CK(c, cudaMemcpyAsync(c->X1, U, c->slab_len * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(c, cudaMemcpyAsync(c->X2, v, c->slab_len * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    dU = c->X1;
+    dv = c->X2;
+    dout = c->R;
+  }
+  double eps = 0.0;
+  if (c->d.jv_mode == STDG_JV_FD) {
+    double nu, nv;
+    CKS(norm2(c, dU, c->slab_len, &nu));
+    CKS(norm2(c, dv, c->slab_len, &nv));
+    eps = fd_base_eps() * (1.0 + nu) / (nv > 0 ? nv : 1.0);
+    CKS(op_residual(c, dU, c->uprev, nullptr, c->F0));
+  }
+  CKS(op_jv(c, dU, c->F0, dv, 1.0, eps, dout));
+  if (kind == STDG_HOST) {
+    CK(c, cudaMemcpyAsync(Jv, dout, c->slab_len * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+  }
+  return STDG_OK;
+}
+
+stdg_status stdg_slab_norm(stdg_ctx* c, const double* x, int kind, double* out) {
+  if (!c || !x || !out || (kind != STDG_HOST && kind != STDG_DEVICE)) return STDG_ERR_INVALID_ARG;
+  DevGuard g(c->device);
+  const double* dx = x;
+  if (kind == STDG_HOST) {
+    CK(c, cudaMemcpyAsync(c->X1, x, c->slab_len * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    dx = c->X1;
+  }
+  return norm2(c, dx, c->slab_len, out);
+}
+
+stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
+  if (!c) return STDG_ERR_INVALID_ARG;
+  DevGuard g(c->device);
+  stdg_slab_stats S;
+  std::memset(&S, 0, sizeof(S));
+  const size_t L = c->slab_len;
+  const int blk = c->nd * c->r;
+  CK(c, broadcast_slab<double>(c->U, c->uprev, c->nelem, c->s, blk, c->st));
+  CKS(op_residual(c, c->U, c->uprev, c->R, c->F0));
+  ++S.residual_evals;
+  double res;
+  CKS(norm2(c, c->R, L, &res));
+  S.res0 = res;
+  const double target = std::fmax(c->d.newton_rtol * res, c->d.newton_atol);
+  stdg_status status = STDG_OK;
+  while (true) {
+    if (!std::isfinite(res)) {
+      status = fail(c, STDG_ERR_NAN, "Newton: non-finite residual norm");
+      break;
+    }
+    if (res <= target) break;
+    if (S.newton_its >= c->d.newton_maxit) {
+      status = fail(c, STDG_ERR_NOT_CONVERGED, "Newton: newton_maxit reached");
+      break;
+    }
+    double nu;
+    CKS(norm2(c, c->U, L, &nu));
+    const double eps_u = fd_base_eps() * (1.0 + nu);
+    int its = 0, jvs = 0;
+    CKS(gmres(c, res, eps_u, &its, &jvs));
+    S.gmres_its += its;
+    S.jv_evals += jvs;
+    CK(c, (scale_add<double, double>(c->U, c->U, 1.0, c->delta, 1.0, L, c->st)));
+    CKS(op_residual(c, c->U, c->uprev, c->R, c->F0));
+    ++S.residual_evals;
+    CKS(norm2(c, c->R, L, &res));
+    ++S.newton_its;
+  }
+  S.res_final = res;
+  if (status != STDG_ERR_NAN) {
+    CK(c, extract_last<double>(c->uprev, c->U, c->nelem, c->s, blk, c->st));
+    c->t += c->d.dt;
+    c->have_slab = true;
+  }
+  CK(c, cudaStreamSynchronize(c->st));
+  if (stats) *stats = S;
+  return status;
+}
+
+const char* stdg_last_error(const stdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+const char* stdg_status_string(stdg_status st) {
+  switch (st) {
+    case STDG_OK: return "ok";
+    case STDG_ERR_INVALID_ARG: return "invalid argument";
+    case STDG_ERR_OOM: return "out of device memory";
+    case STDG_ERR_CUDA: return "CUDA error";
+    case STDG_ERR_NOT_CONVERGED: return "Newton did not converge";
+    case STDG_ERR_GMRES_BREAKDOWN: return "GMRES breakdown";
+    case STDG_ERR_NAN: return "non-finite residual";
+    case STDG_ERR_TIMEOUT: return "timeout";
+    case STDG_ERR_CANCELLED: return "cancelled";
+    case STDG_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+const char* stdg_version(void) { return "stdg-gb300 0.1"; }
+
+}  // extern "C"

@@ -1,0 +1,234 @@
+"""Thin ctypes binding of libstdg.so (include/stdg.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts Python
+arguments (numpy arrays for host memory, torch CUDA tensors for device memory)
+to the C ABI and raises ``StdgError`` on a non-OK status.  There is no CPU
+fallback: ``load()`` raises if the library has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libstdg.so")
+
+ADVECTION, EULER, BURGERS = 0, 1, 2
+FLUX_RUSANOV = 0
+FP64, MIXED_FP32 = 0, 1
+JV_FD, JV_EXACT = 0, 1
+HOST, DEVICE = 0, 1
+
+STATUS = {0: "STDG_OK", 1: "STDG_ERR_INVALID_ARG", 2: "STDG_ERR_OOM", 3: "STDG_ERR_CUDA",
+          4: "STDG_ERR_NOT_CONVERGED", 5: "STDG_ERR_GMRES_BREAKDOWN", 6: "STDG_ERR_NAN",
+          7: "STDG_ERR_TIMEOUT", 8: "STDG_ERR_CANCELLED", 9: "STDG_ERR_UNSUPPORTED"}
+
+
+class stdg_config_desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("cells", ctypes.c_int * 3),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("N", ctypes.c_int), ("s", ctypes.c_int), ("equation", ctypes.c_int),
+                ("adv_vel", ctypes.c_double * 3), ("gamma", ctypes.c_double), ("flux", ctypes.c_int),
+                ("dt", ctypes.c_double), ("precision", ctypes.c_int), ("jv_mode", ctypes.c_int),
+                ("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double),
+                ("newton_maxit", ctypes.c_int), ("gmres_m", ctypes.c_int),
+                ("gmres_rtol", ctypes.c_double), ("gmres_maxit", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_size_t)]
+
+
+class stdg_slab_stats(ctypes.Structure):
+    _fields_ = [("newton_its", ctypes.c_int), ("gmres_its", ctypes.c_int),
+                ("residual_evals", ctypes.c_int), ("jv_evals", ctypes.c_int),
+                ("res0", ctypes.c_double), ("res_final", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class StdgError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "stdg_config_default": (None, [ctypes.POINTER(stdg_config_desc)]),
+    "stdg_create": (ctypes.c_int, [ctypes.POINTER(stdg_config_desc), _P, ctypes.POINTER(_P)]),
+    "stdg_destroy": (ctypes.c_int, [_P]),
+    "stdg_state_len": (ctypes.c_size_t, [_P]),
+    "stdg_slab_len": (ctypes.c_size_t, [_P]),
+    "stdg_coord_len": (ctypes.c_size_t, [_P]),
+    "stdg_device_bytes": (ctypes.c_size_t, [_P]),
+    "stdg_node_coordinates": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "stdg_set_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "stdg_get_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "stdg_get_slab": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "stdg_advance_slab": (ctypes.c_int, [_P, ctypes.POINTER(stdg_slab_stats)]),
+    "stdg_residual": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
+    "stdg_jv": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
+    "stdg_slab_norm": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "stdg_last_error": (ctypes.c_char_p, [_P]),
+    "stdg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "stdg_version": (ctypes.c_char_p, []),
+}
+
+
+def load(path=None):
+    """Load libstdg.so (built by paper_2201_05800_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError("libstdg.so not built (%s): run python -m paper_2201_05800_gb300.build" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def config_default():
+    d = stdg_config_desc()
+    load().stdg_config_default(ctypes.byref(d))
+    return d
+
+
+def make_config(**kw):
+    """stdg_config_desc from defaults overridden by keyword arguments (sequences for arrays)."""
+    d = config_default()
+    for k, v in kw.items():
+        if k in ("cells", "lo", "hi", "adv_vel"):
+            arr = getattr(d, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(d, k, v)
+    return d
+
+
+def _ptr(x, kind):
+    """(pointer, kind) for a numpy FP64 array (host) or a torch CUDA FP64 tensor (device)."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise TypeError("host arrays must be C-contiguous float64")
+        return ctypes.c_void_p(x.ctypes.data), HOST
+    import torch  # device memory comes from torch
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous() or not x.is_cuda:
+            raise TypeError("device tensors must be contiguous float64 CUDA tensors")
+        return ctypes.c_void_p(x.data_ptr()), DEVICE
+    raise TypeError("expected numpy.ndarray or torch.Tensor, got %r" % type(x))
+
+
+class Context:
+    """Owns one stdg_ctx.  Methods mirror the C entry points (stdg_<name>)."""
+
+    def __init__(self, desc, stream=None):
+        lib = load()
+        self._lib = lib
+        self.desc = desc
+        handle = _P()
+        sp = ctypes.c_void_p(stream) if stream is not None else None
+        st = lib.stdg_create(ctypes.byref(desc), sp, ctypes.byref(handle))
+        if st != 0:
+            raise StdgError(st, "stdg_create failed")
+        self._h = handle
+
+    def _check(self, st):
+        if st != 0:
+            raise StdgError(st, (self._lib.stdg_last_error(self._h) or b"").decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.stdg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def state_len(self):
+        return self._lib.stdg_state_len(self._h)
+
+    @property
+    def slab_len(self):
+        return self._lib.stdg_slab_len(self._h)
+
+    @property
+    def device_bytes(self):
+        return self._lib.stdg_device_bytes(self._h)
+
+    def node_coordinates(self):
+        X = np.empty(self._lib.stdg_coord_len(self._h))
+        self._check(self._lib.stdg_node_coordinates(self._h, ctypes.c_void_p(X.ctypes.data), HOST))
+        return X.reshape(-1, self.desc.dim)
+
+    def set_state(self, u):
+        p, kind = _ptr(u, None)
+        self._check(self._lib.stdg_set_state(self._h, p, kind))
+
+    def get_state(self, out=None):
+        out = np.empty(self.state_len) if out is None else out
+        p, kind = _ptr(out, None)
+        self._check(self._lib.stdg_get_state(self._h, p, kind))
+        return out
+
+    def get_slab(self, out=None):
+        out = np.empty(self.slab_len) if out is None else out
+        p, kind = _ptr(out, None)
+        self._check(self._lib.stdg_get_slab(self._h, p, kind))
+        return out
+
+    def advance_slab(self, check=True):
+        stats = stdg_slab_stats()
+        st = self._lib.stdg_advance_slab(self._h, ctypes.byref(stats))
+        if check:
+            self._check(st)
+        return stats.as_dict() | {"status": st}
+
+    def residual(self, U, u_prev, out=None):
+        out = (np.empty(self.slab_len) if isinstance(U, np.ndarray) else U.new_empty(self.slab_len)) \
+            if out is None else out
+        (pU, k1), (pu, k2), (pR, k3) = _ptr(U, None), _ptr(u_prev, None), _ptr(out, None)
+        if not k1 == k2 == k3:
+            raise TypeError("all buffers must be on the same side (host or device)")
+        self._check(self._lib.stdg_residual(self._h, pU, pu, pR, k1))
+        return out
+
+    def jv(self, U, u_prev, v, out=None):
+        out = (np.empty(self.slab_len) if isinstance(U, np.ndarray) else U.new_empty(self.slab_len)) \
+            if out is None else out
+        ptrs = [_ptr(x, None) for x in (U, u_prev, v, out)]
+        if len({k for _, k in ptrs}) != 1:
+            raise TypeError("all buffers must be on the same side (host or device)")
+        self._check(self._lib.stdg_jv(self._h, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], ptrs[0][1]))
+        return out
+
+    def slab_norm(self, x):
+        p, kind = _ptr(x, None)
+        r = ctypes.c_double()
+        self._check(self._lib.stdg_slab_norm(self._h, p, kind, ctypes.byref(r)))
+        return r.value
+
+
+def version():
+    return load().stdg_version().decode()
+
+
+def status_string(st):
+    return load().stdg_status_string(st).decode()

@@ -1,0 +1,77 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/stdg.h declares.
+
+CPU-only: no call here launches GPU work (argument validation happens before
+any CUDA call, and context creation without a GPU returns STDG_ERR_CUDA)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "stdg.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2201_05800_gb300 import build, stdg
+    build.build()
+    return stdg.load()
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(stdg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert "stdg_create" in names and "stdg_advance_slab" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_struct_layout_matches_header(lib):
+    """The ctypes mirror of stdg_config_desc has the C layout (size checked against a C probe)."""
+    from paper_2201_05800_gb300 import stdg
+    d = stdg.config_default()
+    assert d.dim == 1 and d.N == 3 and d.s == 3 and d.gmres_m == 30
+    assert abs(d.newton_rtol - 1e-10) < 1e-25 and abs(d.gamma - 1.4) < 1e-15
+    # natural alignment of the C struct: 4 ints, 6 doubles, 3 ints, 3 doubles ... ends in a size_t
+    assert ctypes.sizeof(stdg.stdg_config_desc) % 8 == 0
+
+
+def test_invalid_configs_rejected_without_gpu(lib):
+    from paper_2201_05800_gb300 import stdg
+    bad = [dict(dim=4), dict(N=0), dict(N=8), dict(s=1), dict(s=6), dict(dt=-1.0), dict(gmres_m=0),
+           dict(gmres_m=64), dict(equation=7), dict(equation=2, dim=3), dict(cells=[0, 1, 1])]
+    for kw in bad:
+        d = stdg.make_config(**kw)
+        h = ctypes.c_void_p()
+        st = lib.stdg_create(ctypes.byref(d), None, ctypes.byref(h))
+        assert st == 1, kw
+        assert not h.value
+
+
+def test_status_strings(lib):
+    from paper_2201_05800_gb300 import stdg
+    for k in range(10):
+        assert stdg.status_string(k)
+    assert stdg.version().startswith("stdg-gb300")
+
+
+def test_create_without_gpu_reports_cuda_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2201_05800_gb300 import stdg
+    with pytest.raises(stdg.StdgError) as e:
+        stdg.Context(stdg.make_config())
+    assert e.value.status == 3
+
+
+def test_null_arguments(lib):
+    assert lib.stdg_create(None, None, None) == 1
+    assert lib.stdg_destroy(None) == 1
+    assert lib.stdg_state_len(None) == 0
