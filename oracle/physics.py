@@ -23,8 +23,10 @@ ADVECTION, EULER, BURGERS = "advection", "euler", "burgers"
 
 
 def re_abs(x):
-    """|x| evaluated on the real part, complex-step safe."""
-    return x * np.sign(np.real(x))
+    """|x| evaluated on the real part, complex-step safe.  At Re x = 0 the derivative is
+    taken from the x >= 0 branch (|x| is not differentiable there; the paper is silent,
+    this reading matches the tie rule of re_max)."""
+    return np.where(np.real(x) >= 0, x, -x)
 
 
 def re_max(a, b):
