@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark: JFNK slab solves of the 2D Euler isentropic vortex on one GB300.
+
+Workload (the paper's 2D Euler vortex, Sec. 7.3, on the periodic box [0,10]^2):
+64 x 64 quadrilaterals, N = 4 (5 x 5 LGL nodes), N_tau = s = 4, Rusanov flux,
+CFL 0.5 (dt = 0.5 h / max(|v| + c) over the initial LGL nodes, held fixed),
+Newton rtol 1e-10 with GMRES(30), FP64 plain path.  Synthetic analytic data.
+
+One step = one slab solve (stdg_advance_slab): the whole hot path (residual,
+Jacobian-vector products, Gram-Schmidt, Newton updates) over one slab of
+1,638,400 space-time DOF; steps march consecutive slabs.
+
+Reported value: space-time GDOF of residual evaluations per second over the
+timed slab solves (every FP64 residual and every Jacobian-vector product -- a
+residual evaluation at U + eps v -- counts DOF_st), i.e. the effective residual
+throughput of the whole solver; slab solves/s and the kernel-level numbers are
+extra keys.  --impl reference runs the FP64 CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "space-time GDOF residual evals/s + slab solves/s, p50/p99 latency vs plain GPU"
+UNIT = "GDOF/s"
+WORKLOAD = dict(dim=2, cells=(64, 64), lo=(0.0, 0.0), hi=(10.0, 10.0), N=4, s=4, gamma=1.4, cfl=0.5,
+                newton_rtol=1e-10, gmres_m=30, gmres_rtol=1e-3)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x FP64 FMA/clk/SM x flop/FMA x max SM clock
+HBM_PEAK_GBS = 6767.7
+
+
+def _workload_name():
+    w = WORKLOAD
+    return "2D Euler isentropic vortex, %dx%d quads on [0,10]^2, N=%d, s=%d, CFL %.1f, JFNK GMRES(%d), " \
+           "Newton rtol %g, FP64" % (w["cells"][0], w["cells"][1], w["N"], w["s"], w["cfl"], w["gmres_m"],
+                                     w["newton_rtol"])
+
+
+def _vortex_state(coords):
+    from paper_2201_05800_gb300 import inputs
+    return inputs.isentropic_vortex(coords[:, 0], coords[:, 1], gamma=WORKLOAD["gamma"], center=(5.0, 5.0))
+
+
+def _cfl_dt(u, h):
+    """dt = CFL h / max over nodes and directions of |v_a| + c (initial state)."""
+    import numpy as np
+    g = WORKLOAD["gamma"]
+    rho, m1, m2, E = u[:, 0], u[:, 1], u[:, 2], u[:, 3]
+    p = (g - 1.0) * (E - 0.5 * (m1 * m1 + m2 * m2) / rho)
+    c = np.sqrt(g * p / rho)
+    lam = max(np.max(np.abs(m1 / rho) + c), np.max(np.abs(m2 / rho) + c))
+    return WORKLOAD["cfl"] * h / lam
+
+
+def algorithmic_flops_per_node(eq, d, n, s, mode):
+    """Minimal FP64 flops per space-time node of one operator launch (FMA = 2, div = sqrt = 1);
+    face terms counted once per face (d/n face points per node).  Derivation in the design doc."""
+    r = d + 2 if eq == "euler" else 1
+    if eq == "euler":
+        flux = 1 + (2 * d + 3) + 1 + d * (d + 3)
+        face = 12 * r + (2 * d + 8) + 9
+    else:
+        flux = d
+        face = 12 * r + 3
+    vol = d * r * 2 * (n + 1)
+    time_c = r * 2 * s + r / s
+    if mode == "residual":
+        comb = 2 * r + r / s
+        state = 0
+    else:
+        comb = 4 * r
+        state = 2 * r
+        face += 2 * r
+    return state + flux + vol + time_c + comb + (d / n) * face
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- oracle legs
+
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, %(root)r)
+import numpy as np
+from oracle import dgsem, stdg
+from paper_2201_05800_gb300 import inputs
+w = json.loads(%(w)r)
+g = dgsem.Grid(2, w["cells"], w["lo"], w["hi"], w["N"], "euler", {"gamma": w["gamma"]})
+X = g.coordinates()
+u0 = inputs.isentropic_vortex(X[0], X[1], gamma=w["gamma"], center=(5.0, 5.0))
+U = np.stack([inputs.perturbed(u0, 100 + m, 1e-3) for m in range(w["s"])])
+v = inputs.random_array(U.shape, 7)
+F = lambda x: dgsem.spatial_operator(g, x)
+dt = w["dt"]
+dof = U.size
+times = []
+for step in range(%(steps)d):
+    t0 = time.perf_counter()
+    stdg.stdg_residual(F, U, u0, dt)
+    stdg.jv_exact("stdg", F, U, u0, dt, v)
+    times.append(time.perf_counter() - t0)
+print(json.dumps({"times": times, "dof": dof, "evals_per_step": 2}))
+"""
+
+
+def run_oracle(steps, dt):
+    """Time the FP64 oracle (as it stands) on one host core: per step one residual and one exact
+    (complex-step) Jv evaluation of the full slab.  Returns (per-step seconds, dof, evals/step)."""
+    w = dict(WORKLOAD)
+    w["dt"] = dt
+    code = ORACLE_SNIPPET % {"root": ROOT, "w": json.dumps(w), "steps": steps}
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError("oracle run failed: " + out.stderr[-2000:])
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    return res["times"], res["dof"], res["evals_per_step"]
+
+
+def _default_dt():
+    """dt of the workload, computed with the same CFL rule on the host (no GPU needed)."""
+    import numpy as np
+    from oracle import dgsem
+    g = dgsem.Grid(2, WORKLOAD["cells"], WORKLOAD["lo"], WORKLOAD["hi"], WORKLOAD["N"], "euler",
+                   {"gamma": WORKLOAD["gamma"]})
+    X = g.coordinates()
+    from paper_2201_05800_gb300 import inputs
+    u0 = inputs.isentropic_vortex(X[0], X[1], gamma=WORKLOAD["gamma"], center=(5.0, 5.0)).reshape(-1, 4)
+    return _cfl_dt(u0, min(g.h))
+
+
+def reference_arm(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    dt = _default_dt()
+    times, dof, evals = run_oracle(args.warmup + args.steps, dt)
+    timed = times[args.warmup:]
+    T = sum(timed)
+    value = evals * dof * len(timed) / T / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / len(timed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": _workload_name(), "dof_st": dof, "dt": dt},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step: 1 FP64 residual + 1 complex-step Jv of the full "
+                                       "64x64 N=4 s=4 slab (NumPy oracle, weak form)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2201_05800_gb300 import build, stdg
+    build.build()
+    stdg.load()
+    stream = torch.cuda.Stream()
+    w = WORKLOAD
+    desc = stdg.make_config(dim=2, cells=[w["cells"][0], w["cells"][1], 1], lo=[w["lo"][0], w["lo"][1], 0.0],
+                            hi=[w["hi"][0], w["hi"][1], 1.0], N=w["N"], s=w["s"], equation=stdg.EULER,
+                            gamma=w["gamma"], dt=1.0, newton_rtol=w["newton_rtol"], gmres_m=w["gmres_m"],
+                            gmres_rtol=w["gmres_rtol"], newton_maxit=30, gmres_maxit=600)
+    with torch.cuda.stream(stream):
+        probe = stdg.Context(desc, stream.cuda_stream)
+        coords = probe.node_coordinates()
+        probe.close()
+        u0 = np.ascontiguousarray(_vortex_state(coords)).ravel()
+        h = (w["hi"][0] - w["lo"][0]) / w["cells"][0]
+        dt = _cfl_dt(u0.reshape(-1, 4), h)
+        desc.dt = dt
+        ctx = stdg.Context(desc, stream.cuda_stream)
+        dof = ctx.slab_len
+        ctx.set_state(u0)
+        for _ in range(args.warmup):
+            ctx.advance_slab()
+        # ---- timed region: K consecutive slab solves, in-library kernel timing on
+        ctx.profile_enable(True)
+        ctx.profile_read(reset=True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        lat = []
+        with ClockSampler(local) as clk:
+            _barrier(ws)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                t0 = time.perf_counter()
+                stats.append(ctx.advance_slab())
+                lat.append(time.perf_counter() - t0)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            _barrier(ws)
+        prof = ctx.profile_read(reset=True)
+        ctx.profile_enable(False)
+        ms_total = ev0.elapsed_time(ev1)
+        ms_total = _max_over_ranks(ms_total, ws)
+        evals = sum(st["residual_evals"] + st["jv_evals"] for st in stats)
+        evals_all = _sum_over_ranks(float(evals * dof), ws)
+        value = evals_all / (ms_total * 1e-3) / 1e9
+        solves_per_s = _sum_over_ranks(float(args.steps), ws) / (ms_total * 1e-3)
+
+        # ---- dominant kernel roofline (class with the largest in-solve device time)
+        cls = max(prof, key=lambda k: prof[k]["ms"])
+        n, s = w["N"] + 1, w["s"]
+        nodes = w["cells"][0] * w["cells"][1] * s * n ** 2
+        jv_launch_ms = prof["jv"]["ms"] / max(prof["jv"]["launches"], 1)
+        jv_flops = algorithmic_flops_per_node("euler", 2, n, s, "jv") * nodes
+        achieved = jv_flops / (jv_launch_ms * 1e-3) / 1e12
+        traffic = _ncu_traffic()
+        roofline = {"bound": "alu", "kernel": "st_operator_kernel<2,EULER,f64,JvFD,5,4> (FD Jacobian-vector)",
+                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz "
+                                   "(FMA microbenchmark 1.203 TFLOP/s at 1995 MHz)",
+                    "algorithmic_flops_per_launch": jv_flops, "avg_launch_ms": jv_launch_ms,
+                    "dominant_class": cls}
+        # ---- residual kernel alone (isolated, L2 flushed between launches)
+        dU = torch.from_numpy(np.tile(u0.reshape(-1, 1, n * n * 4), (1, s, 1)).ravel()).cuda()
+        du = torch.from_numpy(u0).cuda()
+        dR = torch.empty_like(dU)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        rt = []
+        for i in range(8):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.residual(dU, du, dR)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rt.append(e0.elapsed_time(e1))
+        r_ms = statistics.median(rt[2:])
+        r_flops = algorithmic_flops_per_node("euler", 2, n, s, "residual") * nodes
+        residual_kernel = {"ms": r_ms, "gdof_per_s": dof / (r_ms * 1e-3) / 1e9,
+                           "tflops_algorithmic": r_flops / (r_ms * 1e-3) / 1e12,
+                           "frac_fp64_peak": r_flops / (r_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                           "hbm_gbs_algorithmic": (2 * dof + dof / s) * 8 / (r_ms * 1e-3) / 1e9}
+        clocks = clk.summary()
+
+        # ---- end to end through the public API with host (pinned) buffers
+        hin = torch.from_numpy(ctx.get_state()).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        hin_np, hout_np = hin.numpy(), hout.numpy()
+        _barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_evals = 0
+        for _ in range(args.steps):
+            ctx.set_state(hin_np)
+            st = ctx.advance_slab()
+            ctx.get_state(hout_np)
+            e2e_evals += st["residual_evals"] + st["jv_evals"]
+            hin_np[:] = hout_np
+        torch.cuda.synchronize()
+        e2e_s = _max_over_ranks(time.perf_counter() - t0, ws)
+        e2e_value = _sum_over_ranks(float(e2e_evals * dof), ws) / e2e_s / 1e9
+        ctx.close()
+
+    lat_ms = sorted(1e3 * x for x in lat)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        try:
+            times, odof, oevals = run_oracle(1 + 20, dt)
+            T = sum(times[1:]) / len(times[1:])
+            cpu = {"value": oevals * odof / T / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "20 x (1 FP64 residual + 1 complex-step Jv) of the full 64x64 N=4 s=4 slab "
+                             "(NumPy oracle, weak form, one thread) after one warm-up; %.1f s" % sum(times[1:])}
+        except Exception as e:  # report, do not hide
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: %s" % e}
+    launches = sum(p["launches"] for p in prof.values())
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": _workload_name(), "dof_st": dof, "dt": dt, "parallelism":
+                           "replicas" if ws > 1 else "single GPU",
+                           "l2": "working set per step > L2 (Krylov basis 31 x 13.1 MB FP64); the isolated "
+                                 "residual timing flushes L2 (256 MB write) before each launch"},
+                "slab_solves_per_s": solves_per_s,
+                "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
+                                                                                   int(0.99 * len(lat_ms)))]},
+                "solver": {"newton_its": [st["newton_its"] for st in stats],
+                           "gmres_its": [st["gmres_its"] for st in stats],
+                           "residual_evals": sum(st["residual_evals"] for st in stats),
+                           "jv_evals": sum(st["jv_evals"] for st in stats)},
+                "kernel_time_ms": {k: v["ms"] for k, v in prof.items()},
+                "kernel_launches": {k: v["launches"] for k, v in prof.items()},
+                "residual_kernel": residual_kernel,
+                "roofline": roofline, "clocks": clocks,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hin.numel() * 8),
+                        "d2h_bytes_per_step": int(hout.numel() * 8)},
+                "gpu_launches": launches, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def _ncu_traffic():
+    """DRAM bytes per launch of the FD Jv kernel from the committed ncu summary, or None."""
+    p = os.path.join(ROOT, "profiles", "jv_fd_euler2d_vortex64.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith("dram_bytes_per_launch:"):
+            try:
+                return float(line.split(":", 1)[1].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -90,7 +90,7 @@ typedef struct {
   double newton_rtol;       /* stop when ||R||_2 <= max(rtol ||R(U0)||_2, atol)          */
   double newton_atol;
   int newton_maxit;         /* >= 1                                                      */
-  int gmres_m;              /* restart length, 1..64                                     */
+  int gmres_m;              /* restart length, 1..31                                     */
   double gmres_rtol;        /* inner tolerance eta (relative to ||R||)                   */
   int gmres_maxit;          /* total inner iterations per Newton step, >= 1              */
   size_t hbm_budget_bytes;  /* 0 = unlimited; else create fails with STDG_ERR_OOM above  */
@@ -146,6 +146,29 @@ stdg_status stdg_jv(stdg_ctx* ctx, const double* U, const double* u_prev, const 
 
 /* ||x||_2 of a device or host vector of slab_len values (FP64 accumulation). */
 stdg_status stdg_slab_norm(stdg_ctx* ctx, const double* x, int ptr_kind, double* out);
+
+/* F(U) at every temporal node: the spatial DG-SEM operator M^-1 L_h (Eq. ode)
+ * applied to each time level of the slab U (slab layout in and out). */
+stdg_status stdg_spatial_operator(stdg_ctx* ctx, const double* U, double* F, int ptr_kind);
+
+/* One finite-difference Jacobian-vector launch exactly as GMRES issues it
+ * (device pointers only): Jv = ((D_tau^T M_tau - e_s e_s^T) (x) I) v
+ * + dt/2 (M_tau (x) I) [F(U + eps v) - F0] / eps, with F0 = F(U) supplied by the
+ * caller (stdg_spatial_operator) and eps > 0. */
+stdg_status stdg_jv_fd_apply(stdg_ctx* ctx, const double* U, const double* F0, const double* v, double eps,
+                             double* Jv);
+
+/* Kernel timing inside the library: when enabled, every kernel launch is
+ * bracketed by CUDA events on the context stream and its device time is
+ * summed per class: 0 space-time residual / F(U), 1 Jacobian-vector product,
+ * 2 Gram-Schmidt and other vector kernels of GMRES, 3 other (slab copies). */
+typedef struct {
+  int launches[4];
+  double ms[4];
+} stdg_profile;
+stdg_status stdg_profile_enable(stdg_ctx* ctx, int on);
+/* Synchronises the context stream, returns the sums since the last reset. */
+stdg_status stdg_profile_read(stdg_ctx* ctx, stdg_profile* out, int reset);
 
 const char* stdg_last_error(const stdg_ctx* ctx);
 const char* stdg_status_string(stdg_status st);

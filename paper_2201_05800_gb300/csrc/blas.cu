@@ -11,88 +11,55 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block-reduce `cnt` accumulators (cnt <= kMaxDots + 1) and store them at out[0..cnt).
-template <int NACC>
-__device__ __forceinline__ void block_store(double (&acc)[NACC], int cnt, double* out) {
-  __shared__ double red[kRedThreads / 32][NACC];
+// Block-reduce K accumulators and store them at out[0..K).
+template <int K>
+__device__ __forceinline__ void block_store(const double (&acc)[K], double* out) {
+  __shared__ double red[kRedThreads / 32][K];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < NACC; ++i) {
-    if (i < cnt) {
-      double v = warp_sum(acc[i]);
-      if (lane == 0) red[wid][i] = v;
-    }
+  for (int i = 0; i < K; ++i) {
+    double v = warp_sum(acc[i]);
+    if (lane == 0) red[wid][i] = v;
   }
   __syncthreads();
-  if (threadIdx.x < cnt) {
+  if (threadIdx.x < K) {
     double v = 0.0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[q][threadIdx.x];
     out[threadIdx.x] = v;
   }
 }
 
-template <class TV, class TW>
-__global__ void __launch_bounds__(kRedThreads) multidot_kernel(const TV* __restrict__ V, size_t ld, int k,
+template <class TV, class TW, int K>
+__global__ void __launch_bounds__(kRedThreads) multidot_kernel(const TV* __restrict__ V, size_t ld,
                                                                const TW* __restrict__ w, size_t L,
                                                                double* __restrict__ partials) {
-  double acc[kMaxDots];
+  double acc[K];
 #pragma unroll
-  for (int i = 0; i < kMaxDots; ++i) acc[i] = 0.0;
+  for (int i = 0; i < K; ++i) acc[i] = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < L; idx += stride) {
     const double wv = (double)w[idx];
 #pragma unroll
-    for (int i = 0; i < kMaxDots; ++i)
-      if (i < k) acc[i] = fma((double)V[(size_t)i * ld + idx], wv, acc[i]);
+    for (int i = 0; i < K; ++i) acc[i] = fma((double)V[(size_t)i * ld + idx], wv, acc[i]);
   }
-  block_store(acc, k, partials + (size_t)blockIdx.x * kPartialStride);
+  block_store<K>(acc, partials + (size_t)blockIdx.x * kPartialStride);
 }
 
-template <class TV, class TW, bool DOTS, bool NORM>
+template <class TV, class TW>
 __global__ void __launch_bounds__(kRedThreads) update_kernel(TW* __restrict__ w, const TV* __restrict__ V, size_t ld,
-                                                             int k, const double* __restrict__ coef, double sign,
-                                                             size_t L, double* __restrict__ partials) {
-  __shared__ double c[kMaxDots];
-  if (threadIdx.x < kMaxDots) c[threadIdx.x] = threadIdx.x < k ? sign * coef[threadIdx.x] : 0.0;
-  __syncthreads();
-  constexpr int NA = DOTS ? kMaxDots + 1 : 1;
-  double acc[NA];
-#pragma unroll
-  for (int i = 0; i < NA; ++i) acc[i] = 0.0;
+                                                             int k, const __grid_constant__ Coefs c, size_t L) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < L; idx += stride) {
-    double v[kMaxDots];
-    double x = (double)w[idx];
-#pragma unroll
-    for (int i = 0; i < kMaxDots; ++i)
-      if (i < k) {
-        v[i] = (double)V[(size_t)i * ld + idx];
-        x = fma(-c[i], v[i], x);
-      }
-    const TW xs = (TW)x;
-    w[idx] = xs;
-    const double xr = (double)xs;
-    if (DOTS) {
-#pragma unroll
-      for (int i = 0; i < kMaxDots; ++i)
-        if (i < k) acc[i] = fma(v[i], xr, acc[i]);
-      acc[NA - 1] = fma(xr, xr, acc[NA - 1]);
-    } else if (NORM) {
-      acc[0] = fma(xr, xr, acc[0]);
+    double x0 = (double)w[idx], x1 = 0.0, x2 = 0.0, x3 = 0.0;
+    int i = 0;
+    for (; i + 4 <= k; i += 4) {
+      x0 = fma(-c.c[i], (double)V[(size_t)i * ld + idx], x0);
+      x1 = fma(-c.c[i + 1], (double)V[(size_t)(i + 1) * ld + idx], x1);
+      x2 = fma(-c.c[i + 2], (double)V[(size_t)(i + 2) * ld + idx], x2);
+      x3 = fma(-c.c[i + 3], (double)V[(size_t)(i + 3) * ld + idx], x3);
     }
-  }
-  if (DOTS || NORM) {
-    double* out = partials + (size_t)blockIdx.x * kPartialStride;
-    if (DOTS) {
-      // dots at [0, k), norm^2 at k
-      double a2[kMaxDots + 1];
-#pragma unroll
-      for (int i = 0; i < kMaxDots + 1; ++i) a2[i] = (i < k) ? acc[i] : (i == k ? acc[NA - 1] : 0.0);
-      block_store(a2, k + 1, out);
-    } else {
-      double a1[1] = {acc[0]};
-      block_store(a1, 1, out);
-    }
+    for (; i < k; ++i) x0 = fma(-c.c[i], (double)V[(size_t)i * ld + idx], x0);
+    w[idx] = (TW)((x0 + x1) + (x2 + x3));
   }
 }
 
@@ -150,26 +117,35 @@ unsigned grid_for(size_t L) {
   return (unsigned)b;
 }
 
+template <class TV, class TW, int K>
+cudaError_t multidot_k(const TV* V, size_t ld, const TW* w, size_t L, double* partials, int nblk, cudaStream_t st) {
+  multidot_kernel<TV, TW, K><<<nblk, kRedThreads, 0, st>>>(V, ld, w, L, partials);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 template <class TV, class TW>
 cudaError_t multidot(const TV* V, size_t ld, int k, const TW* w, size_t L, double* partials, int nblk,
                      cudaStream_t st) {
-  if (k < 1 || k > kMaxDots) return cudaErrorInvalidValue;
-  multidot_kernel<TV, TW><<<nblk, kRedThreads, 0, st>>>(V, ld, k, w, L, partials);
-  return cudaGetLastError();
+#define STDG_DOT_CASE(K) \
+  case K: return multidot_k<TV, TW, K>(V, ld, w, L, partials, nblk, st);
+  switch (k) {
+    STDG_DOT_CASE(1) STDG_DOT_CASE(2) STDG_DOT_CASE(3) STDG_DOT_CASE(4) STDG_DOT_CASE(5) STDG_DOT_CASE(6)
+    STDG_DOT_CASE(7) STDG_DOT_CASE(8) STDG_DOT_CASE(9) STDG_DOT_CASE(10) STDG_DOT_CASE(11) STDG_DOT_CASE(12)
+    STDG_DOT_CASE(13) STDG_DOT_CASE(14) STDG_DOT_CASE(15) STDG_DOT_CASE(16) STDG_DOT_CASE(17) STDG_DOT_CASE(18)
+    STDG_DOT_CASE(19) STDG_DOT_CASE(20) STDG_DOT_CASE(21) STDG_DOT_CASE(22) STDG_DOT_CASE(23) STDG_DOT_CASE(24)
+    STDG_DOT_CASE(25) STDG_DOT_CASE(26) STDG_DOT_CASE(27) STDG_DOT_CASE(28) STDG_DOT_CASE(29) STDG_DOT_CASE(30)
+    STDG_DOT_CASE(31) STDG_DOT_CASE(32)
+    default: return cudaErrorInvalidValue;
+  }
+#undef STDG_DOT_CASE
 }
 
 template <class TV, class TW>
-cudaError_t update(TW* w, const TV* V, size_t ld, int k, const double* coef, double coef_sign, size_t L,
-                   double* partials, int nblk, bool dots, bool norm, cudaStream_t st) {
-  if (k < 0 || k > kMaxDots) return cudaErrorInvalidValue;
-  if (dots)
-    update_kernel<TV, TW, true, true><<<nblk, kRedThreads, 0, st>>>(w, V, ld, k, coef, coef_sign, L, partials);
-  else if (norm)
-    update_kernel<TV, TW, false, true><<<nblk, kRedThreads, 0, st>>>(w, V, ld, k, coef, coef_sign, L, partials);
-  else
-    update_kernel<TV, TW, false, false><<<nblk, kRedThreads, 0, st>>>(w, V, ld, k, coef, coef_sign, L, partials);
+cudaError_t update(TW* w, const TV* V, size_t ld, int k, const Coefs& c, size_t L, cudaStream_t st) {
+  if (k < 1 || k > kMaxDots) return cudaErrorInvalidValue;
+  update_kernel<TV, TW><<<grid_for(L), kRedThreads, 0, st>>>(w, V, ld, k, c, L);
   return cudaGetLastError();
 }
 
@@ -199,9 +175,9 @@ cudaError_t extract_last(T* u, const T* U, long long nelem, int s, int blk, cuda
 
 template cudaError_t multidot<double, double>(const double*, size_t, int, const double*, size_t, double*, int, cudaStream_t);
 template cudaError_t multidot<float, float>(const float*, size_t, int, const float*, size_t, double*, int, cudaStream_t);
-template cudaError_t update<double, double>(double*, const double*, size_t, int, const double*, double, size_t, double*, int, bool, bool, cudaStream_t);
-template cudaError_t update<float, float>(float*, const float*, size_t, int, const double*, double, size_t, double*, int, bool, bool, cudaStream_t);
-template cudaError_t update<float, double>(double*, const float*, size_t, int, const double*, double, size_t, double*, int, bool, bool, cudaStream_t);
+template cudaError_t update<double, double>(double*, const double*, size_t, int, const Coefs&, size_t, cudaStream_t);
+template cudaError_t update<float, float>(float*, const float*, size_t, int, const Coefs&, size_t, cudaStream_t);
+template cudaError_t update<float, double>(double*, const float*, size_t, int, const Coefs&, size_t, cudaStream_t);
 template cudaError_t scale_add<double, double>(double*, const double*, double, const double*, double, size_t, cudaStream_t);
 template cudaError_t scale_add<double, float>(float*, const double*, double, const double*, double, size_t, cudaStream_t);
 template cudaError_t scale_add<float, float>(float*, const float*, double, const float*, double, size_t, cudaStream_t);

@@ -1,12 +1,14 @@
 // Vector kernels of the Newton-GMRES slab solver: batched dot products for
-// Gram-Schmidt (V^T w), the fused update w -= V c (with the dots of the
-// updated w against V and its squared norm, so that the classical
-// Gram-Schmidt re-orthogonalisation pass costs no extra read), linear
-// combinations x += V y, and slab utilities.
+// Gram-Schmidt (V^T w, with |w|^2 when w is the last row), the update
+// w -= sum_i c_i V_i with the coefficients passed by value, and slab
+// utilities.
 //
 // Reductions are deterministic: a fixed grid (independent of the vector
 // length) writes per-block partial sums in a fixed order, and a second kernel
-// sums the partials in a fixed tree.  FP64 accumulation throughout.
+// sums the partials in a fixed tree.  FP64 accumulation throughout.  The dot
+// kernel is instantiated for every row count 1..kMaxDots so that no FP64
+// instruction is issued for an absent row (predicated-off FP64 instructions
+// still occupy the FP64 pipe).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -15,24 +17,27 @@
 namespace stdg {
 
 constexpr int kRedThreads = 256;
-constexpr int kMaxDots = 32;   // dot products per pass held in registers
-constexpr int kPartialStride = 72;  // doubles per block in the partials buffer (>= kMaxDots+1, x8 aligned)
+constexpr int kMaxDots = 32;        // rows per dot pass (Krylov basis + the new vector)
+constexpr int kPartialStride = 40;  // doubles per block in the partials buffer (>= kMaxDots)
 
-// partials[b*kPartialStride + i] = sum over block b of scale(V_i) . w (i < k <= kMaxDots)
+// Coefficients of an update, passed by value in the kernel parameters.
+struct Coefs {
+  double c[kMaxDots];
+};
+
+// partials[b*kPartialStride + i] = sum over block b of V_i . w   (i < k <= kMaxDots)
 template <class TV, class TW>
 cudaError_t multidot(const TV* V, size_t ld, int k, const TW* w, size_t L, double* partials, int nblk,
                      cudaStream_t st);
 
-// w -= sum_i coef[i] V_i (i < k); if dots: partials also receive V_i . w_new (i < k) and
-// |w_new|^2 at index k; else only |w_new|^2 at index 0 when norm is set.
+// w -= sum_{i<k} c.c[i] V_i   (k <= kMaxDots)
 template <class TV, class TW>
-cudaError_t update(TW* w, const TV* V, size_t ld, int k, const double* coef, double coef_sign, size_t L,
-                   double* partials, int nblk, bool dots, bool norm, cudaStream_t st);
+cudaError_t update(TW* w, const TV* V, size_t ld, int k, const Coefs& c, size_t L, cudaStream_t st);
 
 // out[i] = sum_b partials[b*kPartialStride + i] for i < count (one block per output).
 cudaError_t reduce_partials(const double* partials, int nblk, int count, double* out, cudaStream_t st);
 
-// y = a * x (+ b * z if z)
+// y = a * x (+ b * z if z); y may alias x or z
 template <class TX, class TY>
 cudaError_t scale_add(TY* y, const TX* x, double a, const TX* z, double b, size_t L, cudaStream_t st);
 

@@ -43,6 +43,7 @@ struct OpArgs {
   T gamma;
   T adv[3];
   T eps;                   // FD step (kModeJvFD)
+  T inv_eps;               // 1 / eps
   T vscale;                // v is read as vscale * v (kModeJvFD / kModeJvExact)
   const T* U;              // slab, [e][m][node][c]
   const T* v;              // direction, same layout
@@ -103,6 +104,19 @@ struct Phys<STDG_ADVECTION, DIM> {
   __device__ static void flux(const V* u, int a, V* f, const OpArgs<T>& k) { f[0] = k.adv[a] * u[0]; }
   template <class V, class T>
   __device__ static V speed(const V* u, int a, const OpArgs<T>& k) { return Lift<V, T>::from(fabs(k.adv[a])); }
+  template <class V, class T>
+  __device__ static void flux_all_speed(const V* u, V (*f)[R], V* lam, const OpArgs<T>& k) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      f[a][0] = k.adv[a] * u[0];
+      lam[a] = Lift<V, T>::from(fabs(k.adv[a]));
+    }
+  }
+  template <class V, class T>
+  __device__ static V flux_speed(const V* u, int a, V* f, const OpArgs<T>& k) {
+    f[0] = k.adv[a] * u[0];
+    return Lift<V, T>::from(fabs(k.adv[a]));
+  }
 };
 
 template <int DIM>
@@ -118,6 +132,21 @@ struct Phys<STDG_BURGERS, DIM> {
   __device__ static void flux(const V* u, int a, V* f, const OpArgs<T>& k) { f[0] = T(0.5) * (u[0] * u[0]); }
   template <class V, class T>
   __device__ static V speed(const V* u, int a, const OpArgs<T>& k) { return dabs(u[0]); }
+  template <class V, class T>
+  __device__ static void flux_all_speed(const V* u, V (*f)[R], V* lam, const OpArgs<T>& k) {
+    V h = T(0.5) * (u[0] * u[0]);
+    V l = dabs(u[0]);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      f[a][0] = h;
+      lam[a] = l;
+    }
+  }
+  template <class V, class T>
+  __device__ static V flux_speed(const V* u, int a, V* f, const OpArgs<T>& k) {
+    f[0] = T(0.5) * (u[0] * u[0]);
+    return dabs(u[0]);
+  }
 };
 
 template <int DIM>
@@ -154,6 +183,35 @@ struct Phys<STDG_EULER, DIM> {
 #pragma unroll
     for (int b = 0; b < DIM; ++b) f[1 + b] = (b == a) ? u[1 + b] * va + p : u[1 + b] * va;
     f[R - 1] = (u[R - 1] + p) * va;
+  }
+  // fluxes in every direction and the wave speeds |v_a| + c, sharing 1/rho, p and c
+  template <class V, class T>
+  __device__ static void flux_all_speed(const V* u, V (*f)[R], V* lam, const OpArgs<T>& k) {
+    V irho = recip(u[0]);
+    V p = pressure(u, irho, k);
+    V Ep = u[R - 1] + p;
+    V c = dsqrt(k.gamma * (p * irho));
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      V va = u[1 + a] * irho;
+      f[a][0] = u[1 + a];
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) f[a][1 + b] = (b == a) ? u[1 + b] * va + p : u[1 + b] * va;
+      f[a][R - 1] = Ep * va;
+      lam[a] = dabs(va) + c;
+    }
+  }
+  // flux in direction a and the wave speed |v_a| + c
+  template <class V, class T>
+  __device__ static V flux_speed(const V* u, int a, V* f, const OpArgs<T>& k) {
+    V irho = recip(u[0]);
+    V p = pressure(u, irho, k);
+    V va = u[1 + a] * irho;
+    f[0] = u[1 + a];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) f[1 + b] = (b == a) ? u[1 + b] * va + p : u[1 + b] * va;
+    f[R - 1] = (u[R - 1] + p) * va;
+    return dabs(va) + dsqrt(k.gamma * (p * irho));
   }
   // |v_a| + sqrt(gamma p / rho)
   template <class V, class T>

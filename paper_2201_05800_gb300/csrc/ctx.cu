@@ -49,6 +49,12 @@ struct stdg_ctx {
   double t = 0.0;
   bool have_slab = false;
   std::string err;
+  // kernel timing (stdg_profile_*)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_live;
+  int prof_launches[4] = {0, 0, 0, 0};
+  double prof_ms[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -64,6 +70,56 @@ struct DevGuard {
   }
 };
 
+cudaEvent_t take_event(stdg_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Brackets one kernel launch with CUDA events when profiling is on.
+struct Prof {
+  stdg_ctx* c;
+  int cls;
+  cudaEvent_t a = nullptr;
+  Prof(stdg_ctx* ctx, int k) : c(ctx), cls(k) {
+    if (c->prof && (a = take_event(c))) cudaEventRecord(a, c->st);
+  }
+  ~Prof() {
+    if (!a) return;
+    cudaEvent_t b = take_event(c);
+    if (!b) {
+      c->ev_pool.push_back(a);
+      return;
+    }
+    cudaEventRecord(b, c->st);
+    c->ev_live.push_back({cls, {a, b}});
+  }
+};
+
+// Sum the recorded launches (the stream must be synchronised) and recycle the events.
+void prof_collect(stdg_ctx* c) {
+  for (auto& x : c->ev_live) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, x.second.first, x.second.second) == cudaSuccess) {
+      c->prof_ms[x.first] += ms;
+      c->prof_launches[x.first] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->ev_pool.push_back(x.second.first);
+    c->ev_pool.push_back(x.second.second);
+  }
+  c->ev_live.clear();
+}
+
 stdg_status fail(stdg_ctx* c, stdg_status st, const std::string& msg) {
   if (c) c->err = msg;
   return st;
@@ -74,6 +130,13 @@ stdg_status fail(stdg_ctx* c, stdg_status st, const std::string& msg) {
     cudaError_t _e = (expr);                                                                          \
     if (_e != cudaSuccess)                                                                            \
       return fail((c), STDG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));            \
+  } while (0)
+
+// CK inside a profiled bracket of class `cls`
+#define PK(c, cls, expr)   \
+  do {                     \
+    Prof _p((c), (cls));   \
+    CK((c), expr);         \
   } while (0)
 
 #define CKS(expr)                        \
@@ -172,6 +235,7 @@ stdg_status op_residual(stdg_ctx* c, const double* U, const double* uprev, doubl
   k.uprev = uprev;
   k.out = out;
   k.fout = fout;
+  Prof p(c, 0);
   CK(c, launch_operator<double>(c->dim, c->d.equation, kModeResidual, k, c->st));
   return STDG_OK;
 }
@@ -186,15 +250,17 @@ stdg_status op_jv(stdg_ctx* c, const double* U, const double* F0, const double* 
   k.F0 = F0;
   k.vscale = vscale;
   k.eps = eps;
+  k.inv_eps = eps > 0.0 ? 1.0 / eps : 0.0;
   k.out = out;
+  Prof p(c, 1);
   CK(c, launch_operator<double>(c->dim, c->d.equation, mode, k, c->st));
   return STDG_OK;
 }
 
 // ---- reductions
 stdg_status dots_to_small(stdg_ctx* c, const double* V, int k, const double* w, int small_off) {
-  CK(c, (multidot<double, double>(V, c->slab_len, k, w, c->slab_len, c->partials, c->nblk, c->st)));
-  CK(c, reduce_partials(c->partials, c->nblk, k, c->small + small_off, c->st));
+  PK(c, 2, (multidot<double, double>(V, c->slab_len, k, w, c->slab_len, c->partials, c->nblk, c->st)));
+  PK(c, 2, reduce_partials(c->partials, c->nblk, k, c->small + small_off, c->st));
   return STDG_OK;
 }
 
@@ -205,8 +271,8 @@ stdg_status fetch_small(stdg_ctx* c, int off, int count) {
 }
 
 stdg_status norm2(stdg_ctx* c, const double* x, size_t L, double* out) {
-  CK(c, (multidot<double, double>(x, L, 1, x, L, c->partials, c->nblk, c->st)));
-  CK(c, reduce_partials(c->partials, c->nblk, 1, c->small + 200, c->st));
+  PK(c, 2, (multidot<double, double>(x, L, 1, x, L, c->partials, c->nblk, c->st)));
+  PK(c, 2, reduce_partials(c->partials, c->nblk, 1, c->small + 200, c->st));
   CKS(fetch_small(c, 200, 1));
   *out = std::sqrt(c->hpin[200]);
   return STDG_OK;
@@ -215,11 +281,18 @@ stdg_status norm2(stdg_ctx* c, const double* x, size_t L, double* out) {
 double fd_base_eps() { return std::sqrt(2.220446049250313e-16); }
 
 // ---- GMRES(m) for J(U) delta = -R, delta accumulated in c->delta.
+//
+// Arnoldi with classical Gram-Schmidt and the DGKS re-orthogonalisation test:
+// one fused pass gives p_i = V_i . w (i <= j) and |w|^2 (w is the row after
+// the basis); |w - V h|^2 = |w|^2 - |h|^2 (Pythagoras); a second projection is
+// made only when that norm fell below |w|/sqrt(2).  Basis rows are stored
+// unnormalised with scale factors sig_i (v_i = sig_i V_i), so no scaling pass
+// is needed; coefficients reach the update kernel by value.
 stdg_status gmres(stdg_ctx* c, double beta0, double eps_u, int* its_out, int* jv_out) {
   const int m = c->d.gmres_m;
   const size_t L = c->slab_len;
   const double tol = c->d.gmres_rtol * beta0;
-  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m), sig(m + 1);
   auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
   auto Vrow = [&](int i) { return c->V + (size_t)i * L; };
   CK(c, cudaMemsetAsync(c->delta, 0, L * sizeof(double), c->st));
@@ -228,17 +301,18 @@ stdg_status gmres(stdg_ctx* c, double beta0, double eps_u, int* its_out, int* jv
   while (its < c->d.gmres_maxit) {
     double beta;
     if (first) {
-      CK(c, (scale_add<double, double>(Vrow(0), c->R, -1.0 / beta0, nullptr, 0.0, L, c->st)));
+      PK(c, 2, (scale_add<double, double>(Vrow(0), c->R, 1.0, nullptr, 0.0, L, c->st)));
       beta = beta0;
+      sig[0] = -1.0 / beta0;  // v_0 = -R / |R|
     } else {
       double nd;
       CKS(norm2(c, c->delta, L, &nd));
       CKS(op_jv(c, c->U, c->F0, c->delta, 1.0, eps_u / (nd > 0 ? nd : 1.0), Vrow(0)));
       ++jvs;
-      CK(c, (scale_add<double, double>(Vrow(0), c->R, -1.0, Vrow(0), -1.0, L, c->st)));
+      PK(c, 2, (scale_add<double, double>(Vrow(0), c->R, -1.0, Vrow(0), -1.0, L, c->st)));
       CKS(norm2(c, Vrow(0), L, &beta));
       if (!(beta > tol)) break;
-      CK(c, (scale_add<double, double>(Vrow(0), Vrow(0), 1.0 / beta, nullptr, 0.0, L, c->st)));
+      sig[0] = 1.0 / beta;
     }
     first = false;
     std::fill(g.begin(), g.end(), 0.0);
@@ -247,20 +321,36 @@ stdg_status gmres(stdg_ctx* c, double beta0, double eps_u, int* its_out, int* jv
     bool done = false;
     for (int j = 0; j < m && its < c->d.gmres_maxit; ++j) {
       double* w = Vrow(j + 1);
-      CKS(op_jv(c, c->U, c->F0, Vrow(j), 1.0, eps_u, w));
+      CKS(op_jv(c, c->U, c->F0, Vrow(j), sig[j], eps_u, w));
       ++jvs;
-      // CGS2: h1 = V^T w; w -= V h1 (and h2 = V^T w); w -= V h2 (and |w|^2)
-      CKS(dots_to_small(c, c->V, j + 1, w, 0));
-      CK(c, (update<double, double>(w, c->V, L, j + 1, c->small, 1.0, L, c->partials, c->nblk, true, true, c->st)));
-      CK(c, reduce_partials(c->partials, c->nblk, j + 1, c->small + 64, c->st));
-      CK(c, (update<double, double>(w, c->V, L, j + 1, c->small + 64, 1.0, L, c->partials, c->nblk, false, true,
-                                    c->st)));
-      CK(c, reduce_partials(c->partials, c->nblk, 1, c->small + 128, c->st));
-      CK(c, cudaMemcpyAsync(c->hpin, c->small, 129 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-      CK(c, cudaStreamSynchronize(c->st));
-      for (int i = 0; i <= j; ++i) Hij(i, j) = c->hpin[i] + c->hpin[64 + i];
-      double hn = std::sqrt(c->hpin[128]);
-      if (!std::isfinite(hn)) return fail(c, STDG_ERR_NAN, "GMRES: non-finite Krylov vector norm");
+      // p_i = V_i . w (i <= j) and |w|^2 in one pass over rows 0..j+1
+      CKS(dots_to_small(c, c->V, j + 2, w, 0));
+      CKS(fetch_small(c, 0, j + 2));
+      double w2 = c->hpin[j + 1], h2 = 0.0;
+      Coefs cf;
+      for (int i = 0; i <= j; ++i) {
+        Hij(i, j) = sig[i] * c->hpin[i];
+        h2 += Hij(i, j) * Hij(i, j);
+        cf.c[i] = sig[i] * Hij(i, j);
+      }
+      PK(c, 2, (update<double, double>(w, c->V, L, j + 1, cf, L, c->st)));
+      double r2 = w2 - h2;
+      if (!(r2 > 0.5 * w2)) {
+        // DGKS: severe cancellation, project once more and take the norm directly
+        CKS(dots_to_small(c, c->V, j + 2, w, 0));
+        CKS(fetch_small(c, 0, j + 2));
+        double e2 = 0.0;
+        for (int i = 0; i <= j; ++i) {
+          double hi = sig[i] * c->hpin[i];
+          Hij(i, j) += hi;
+          e2 += hi * hi;
+          cf.c[i] = sig[i] * hi;
+        }
+        PK(c, 2, (update<double, double>(w, c->V, L, j + 1, cf, L, c->st)));
+        r2 = c->hpin[j + 1] - e2;
+      }
+      if (!std::isfinite(r2) || !std::isfinite(w2)) return fail(c, STDG_ERR_NAN, "GMRES: non-finite Krylov vector");
+      const double hn = std::sqrt(r2 > 0.0 ? r2 : 0.0);
       // apply the previous rotations to the new column, then a new one
       for (int i = 0; i < j; ++i) {
         double t0 = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
@@ -276,25 +366,22 @@ stdg_status gmres(stdg_ctx* c, double beta0, double eps_u, int* its_out, int* jv
       g[j] = cs[j] * g[j];
       ++its;
       kdim = j + 1;
-      if (hn > 0.0) CK(c, (scale_add<double, double>(w, w, 1.0 / hn, nullptr, 0.0, L, c->st)));
+      sig[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
       if (std::fabs(g[j + 1]) <= tol || hn <= 1e-300 * beta0) {
         done = true;
         break;
       }
     }
-    // y = H^-1 g (upper triangular), delta += V y
+    // y = H^-1 g (upper triangular), delta += sum_i y_i sig_i V_i
     for (int i = kdim - 1; i >= 0; --i) {
       double acc = g[i];
       for (int q = i + 1; q < kdim; ++q) acc -= Hij(i, q) * y[q];
       y[i] = acc / Hij(i, i);
     }
     if (kdim > 0) {
-      for (int i = 0; i < kdim; ++i) c->hpin[160 + i] = y[i];
-      CK(c, cudaMemcpyAsync(c->small + 160, c->hpin + 160, kdim * sizeof(double), cudaMemcpyHostToDevice, c->st));
-      CK(c, (update<double, double>(c->delta, c->V, L, kdim, c->small + 160, -1.0, L, c->partials, c->nblk, false,
-                                    false, c->st)));
-      // the pinned y must not be overwritten before the copy has run
-      CK(c, cudaStreamSynchronize(c->st));
+      Coefs cf;
+      for (int i = 0; i < kdim; ++i) cf.c[i] = -y[i] * sig[i];
+      PK(c, 2, (update<double, double>(c->delta, c->V, L, kdim, cf, L, c->st)));
     }
     if (done) break;
   }
@@ -406,6 +493,8 @@ stdg_status stdg_destroy(stdg_ctx* c) {
   if (!c) return STDG_ERR_INVALID_ARG;
   DevGuard g(c->device);
   cudaStreamSynchronize(c->st);
+  prof_collect(c);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   if (c->hpin) cudaFreeHost(c->hpin);
   cudaGetLastError();
@@ -535,7 +624,7 @@ stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
   std::memset(&S, 0, sizeof(S));
   const size_t L = c->slab_len;
   const int blk = c->nd * c->r;
-  CK(c, broadcast_slab<double>(c->U, c->uprev, c->nelem, c->s, blk, c->st));
+  PK(c, 3, broadcast_slab<double>(c->U, c->uprev, c->nelem, c->s, blk, c->st));
   CKS(op_residual(c, c->U, c->uprev, c->R, c->F0));
   ++S.residual_evals;
   double res;
@@ -560,7 +649,7 @@ stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
     CKS(gmres(c, res, eps_u, &its, &jvs));
     S.gmres_its += its;
     S.jv_evals += jvs;
-    CK(c, (scale_add<double, double>(c->U, c->U, 1.0, c->delta, 1.0, L, c->st)));
+    PK(c, 2, (scale_add<double, double>(c->U, c->U, 1.0, c->delta, 1.0, L, c->st)));
     CKS(op_residual(c, c->U, c->uprev, c->R, c->F0));
     ++S.residual_evals;
     CKS(norm2(c, c->R, L, &res));
@@ -568,13 +657,65 @@ stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
   }
   S.res_final = res;
   if (status != STDG_ERR_NAN) {
-    CK(c, extract_last<double>(c->uprev, c->U, c->nelem, c->s, blk, c->st));
+    PK(c, 3, extract_last<double>(c->uprev, c->U, c->nelem, c->s, blk, c->st));
     c->t += c->d.dt;
     c->have_slab = true;
   }
   CK(c, cudaStreamSynchronize(c->st));
+  prof_collect(c);
   if (stats) *stats = S;
   return status;
+}
+
+stdg_status stdg_spatial_operator(stdg_ctx* c, const double* U, double* F, int kind) {
+  if (!c || !U || !F || (kind != STDG_HOST && kind != STDG_DEVICE)) return STDG_ERR_INVALID_ARG;
+  DevGuard g(c->device);
+  if (kind == STDG_DEVICE) return op_residual(c, U, c->uprev, nullptr, F);
+  CK(c, cudaMemcpyAsync(c->X1, U, c->slab_len * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CKS(op_residual(c, c->X1, c->uprev, nullptr, c->X2));
+  CK(c, cudaMemcpyAsync(F, c->X2, c->slab_len * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  return STDG_OK;
+}
+
+stdg_status stdg_jv_fd_apply(stdg_ctx* c, const double* U, const double* F0, const double* v, double eps,
+                             double* Jv) {
+  if (!c || !U || !F0 || !v || !Jv || !(eps > 0.0)) return STDG_ERR_INVALID_ARG;
+  DevGuard g(c->device);
+  OpArgs<double> k = c->a64;
+  k.epb = c->epb64[kModeJvFD];
+  k.U = U;
+  k.v = v;
+  k.F0 = F0;
+  k.vscale = 1.0;
+  k.eps = eps;
+  k.inv_eps = 1.0 / eps;
+  k.out = Jv;
+  Prof p(c, 1);
+  CK(c, launch_operator<double>(c->dim, c->d.equation, kModeJvFD, k, c->st));
+  return STDG_OK;
+}
+
+stdg_status stdg_profile_enable(stdg_ctx* c, int on) {
+  if (!c) return STDG_ERR_INVALID_ARG;
+  c->prof = on != 0;
+  return STDG_OK;
+}
+
+stdg_status stdg_profile_read(stdg_ctx* c, stdg_profile* out, int reset) {
+  if (!c || !out) return STDG_ERR_INVALID_ARG;
+  DevGuard g(c->device);
+  CK(c, cudaStreamSynchronize(c->st));
+  prof_collect(c);
+  for (int i = 0; i < 4; ++i) {
+    out->launches[i] = c->prof_launches[i];
+    out->ms[i] = c->prof_ms[i];
+    if (reset) {
+      c->prof_launches[i] = 0;
+      c->prof_ms[i] = 0.0;
+    }
+  }
+  return STDG_OK;
 }
 
 const char* stdg_last_error(const stdg_ctx* c) { return c ? c->err.c_str() : "null context"; }

@@ -3,11 +3,13 @@
 // One CTA owns `epb` consecutive elements (all s temporal nodes of each).  The
 // element tiles are staged in shared memory (component-planar, padded to an
 // odd node stride), then for every temporal node m:
-//   1. thread per node: f_a(u) for all directions a            -> smem
+//   1. thread per node: f_a(u) and the wave speed |v_a| + c for all
+//      directions a (one reciprocal of rho, one pressure, one sound speed)
 //   2. thread per node: volume term  -sum_a (2/h_a) (D f_a)      -> smem acc
 //   3. thread per face point, one direction a at a time: Rusanov flux with
-//      the neighbour trace (read from global memory / L2) and the strong-form
-//      face correction -(2/h_a)(1/w_end)(H.n - f_a(u).n) added to acc
+//      the neighbour trace (read from global memory / L2; its flux and wave
+//      speed share one reciprocal and one pressure) and the strong-form face
+//      correction -(2/h_a)(1/w_end)(H.n - f_a(u).n) added to acc
 //   4. thread per output value (coalesced): temporal coupling
 //        R_m = sum_j omega_j Dtau[j][m] U_j + [m=0] u_prev - [m=s-1] U_s
 //              + dt/2 omega_m F_m
@@ -15,6 +17,9 @@
 // Strong form of the spatial operator (Sec. 3.1 with the SBP property of
 // Eq. SBP): F_I = -sum_a (2/h_a) [ sum_j D[i_a][j] f_a(u_(I,i_a->j))
 //      + (1/w_N) [i_a = N] (H_a^+ - f_a(u_I)) - (1/w_0) [i_a = 0] (H_a^- - f_a(u_I)) ].
+// The kernel is FP64-pipe bound in FP64 (ncu), so every FP64 operation it
+// can avoid is avoided: 2/h_a is folded into D, 1/eps is a multiplication,
+// wave speeds are computed once per node.
 #pragma once
 
 #include <type_traits>
@@ -46,7 +51,8 @@ __host__ __device__ inline size_t op_smem_bytes(int n, int s, int epb) {
   if (MODE != kModeResidual) b += (size_t)epb * s * R * ndp * sizeof(T);  // v tile
   b += (size_t)epb * DIM * R * ndp * vbytes;                     // fluxes
   b += (size_t)epb * R * ndp * vbytes;                           // accumulators
-  b += (kMaxN * kMaxN + kMaxS * kMaxS) * sizeof(T);              // D and C
+  b += (size_t)epb * DIM * ndp * vbytes;                         // wave speeds
+  b += (3 * kMaxN * kMaxN + kMaxS * kMaxS) * sizeof(T);          // scaled D per direction, C
   return b;
 }
 
@@ -73,10 +79,14 @@ __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant_
   T* sv = su + (size_t)epb * s * R * ndp;                        // [epb][s][R][ndp] (Jv modes)
   V* sf = reinterpret_cast<V*>(MODE == kModeResidual ? sv : sv + (size_t)epb * s * R * ndp);  // [epb][DIM][R][ndp]
   V* sr = sf + (size_t)epb * DIM * R * ndp;                      // [epb][R][ndp]
-  T* sD = reinterpret_cast<T*>(sr + (size_t)epb * R * ndp);      // [n][n]  D
-  T* sC = sD + kMaxN * kMaxN;                                    // [s][s]  C
-  for (int i = threadIdx.x; i < kMaxN * kMaxN; i += blockDim.x) sD[i] = k.D[i / kMaxN][i % kMaxN];
-  for (int i = threadIdx.x; i < kMaxS * kMaxS; i += blockDim.x) sC[i] = k.C[i / kMaxS][i % kMaxS];
+  V* sl = sr + (size_t)epb * R * ndp;                            // [epb][DIM][ndp] wave speeds
+  T* sD = reinterpret_cast<T*>(sl + (size_t)epb * DIM * ndp);    // [3][kMaxN][kMaxN]  (2/h_a) D
+  T* sC = sD + 3 * kMaxN * kMaxN;                                // [kMaxS][kMaxS]  C
+  for (int i = tid; i < 3 * kMaxN * kMaxN; i += nth) {
+    const int a = i / (kMaxN * kMaxN), q = i % (kMaxN * kMaxN);
+    sD[i] = k.ginv[a] * k.D[q / kMaxN][q % kMaxN];
+  }
+  for (int i = tid; i < kMaxS * kMaxS; i += nth) sC[i] = k.C[i / kMaxS][i % kMaxS];
 
   const size_t slab_elem = (size_t)s * nd * R;  // values of one element's slab
   // ---- stage the element tiles (coalesced global reads, planar smem writes)
@@ -99,7 +109,7 @@ __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant_
   int strides[3] = {1, n, n * n};
 
   for (int m = 0; m < s; ++m) {
-    // ---- 1. fluxes at every node of the temporal node m
+    // ---- 1. fluxes and wave speeds at every node of the temporal node m
     for (int t = tid; t < nel * nd; t += nth) {
       int el = t / nd, node = t - el * nd;
       size_t so = ((size_t)(el * s + m) * R) * ndp + node;
@@ -108,12 +118,16 @@ __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant_
       for (int c = 0; c < R; ++c)
         u[c] = eval_state<MODE>(su[so + c * ndp], MODE == kModeResidual ? T(0) : sv[so + c * ndp], k.eps);
       V f[DIM][R];
-      P::flux_all(u, f, k);
+      V lam[DIM];
+      P::flux_all_speed(u, f, lam, k);
       V* sfe = sf + (size_t)el * DIM * R * ndp;
+      V* sle = sl + (size_t)el * DIM * ndp;
 #pragma unroll
-      for (int a = 0; a < DIM; ++a)
+      for (int a = 0; a < DIM; ++a) {
+        sle[a * ndp + node] = lam[a];
 #pragma unroll
         for (int c = 0; c < R; ++c) sfe[(a * R + c) * ndp + node] = f[a][c];
+      }
     }
     __syncthreads();
     // ---- 2. volume term
@@ -128,15 +142,13 @@ __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant_
       for (int a = 0; a < DIM; ++a) {
         const int ia = idx[a];
         const int base = node - ia * strides[a];
-        const T g = k.ginv[a];
+        const T* Da = sD + (a * kMaxN + ia) * kMaxN;
 #pragma unroll
         for (int c = 0; c < R; ++c) {
-          V sum = Lift<V, T>::from(T(0));
 #pragma unroll
           for (int j = 0; j < NPX; ++j) {
-            if (FIXED || j < n) sum = sum + sD[ia * kMaxN + j] * sfe[(a * R + c) * ndp + base + j * strides[a]];
+            if (FIXED || j < n) acc[c] = acc[c] - Da[j] * sfe[(a * R + c) * ndp + base + j * strides[a]];
           }
-          acc[c] = acc[c] - g * sum;
         }
       }
       V* sre = sr + (size_t)el * R * ndp;
@@ -180,9 +192,8 @@ __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant_
           um[c] = eval_state<MODE>(su[so + c * ndp], hasv ? sv[so + c * ndp] : T(0), k.eps);
           up[c] = eval_state<MODE>(k.U[gofs + c], hasv ? k.vscale * k.v[gofs + c] : T(0), k.eps);
         }
-        P::flux(up, a, fp, k);
-        V lm = P::speed(um, a, k);
-        V lp = P::speed(up, a, k);
+        const V lm = sl[((size_t)el * DIM + a) * ndp + own];
+        const V lp = P::flux_speed(up, a, fp, k);
         V* sre = sr + (size_t)el * R * ndp;
         const T g = k.ginv[a] * k.winv_end;
         if (side) {  // uL = u-, uR = u+ ; F -= g (H - f(u-))
@@ -225,7 +236,7 @@ __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant_
           if (k.out) k.out[g] = lin + hw * val(Fv);
           if (k.fout) k.fout[g] = val(Fv);
         } else if (MODE == kModeJvFD) {
-          k.out[g] = lin + hw * ((val(Fv) - k.F0[g]) / k.eps);
+          k.out[g] = lin + hw * ((val(Fv) - k.F0[g]) * k.inv_eps);
         } else {
           k.out[g] = lin + hw * tangent(Fv);
         }

@@ -26,7 +26,8 @@ inline size_t operator_smem_bytes(int dim, int r, size_t tsize, int mode, int n,
   if (mode != kModeResidual) b += (size_t)epb * s * r * ndp * tsize;
   b += (size_t)epb * dim * r * ndp * vbytes;
   b += (size_t)epb * r * ndp * vbytes;
-  b += (size_t)(kMaxN * kMaxN + kMaxS * kMaxS) * tsize;
+  b += (size_t)epb * dim * ndp * vbytes;
+  b += (size_t)(3 * kMaxN * kMaxN + kMaxS * kMaxS) * tsize;
   return b;
 }
 

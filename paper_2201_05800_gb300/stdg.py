@@ -45,6 +45,13 @@ class stdg_slab_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class stdg_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int * 4), ("ms", ctypes.c_double * 4)]
+
+
+PROFILE_CLASSES = ("residual", "jv", "gram_schmidt", "other")
+
+
 class StdgError(RuntimeError):
     def __init__(self, status, msg=""):
         super().__init__("%s: %s" % (STATUS.get(status, status), msg))
@@ -70,6 +77,10 @@ _SIGS = {
     "stdg_residual": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
     "stdg_jv": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
     "stdg_slab_norm": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "stdg_spatial_operator": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "stdg_jv_fd_apply": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, _P]),
+    "stdg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "stdg_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(stdg_profile), ctypes.c_int]),
     "stdg_last_error": (ctypes.c_char_p, [_P]),
     "stdg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "stdg_version": (ctypes.c_char_p, []),
@@ -218,6 +229,31 @@ class Context:
             raise TypeError("all buffers must be on the same side (host or device)")
         self._check(self._lib.stdg_jv(self._h, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], ptrs[0][1]))
         return out
+
+    def spatial_operator(self, U, out=None):
+        out = (np.empty(self.slab_len) if isinstance(U, np.ndarray) else U.new_empty(self.slab_len)) \
+            if out is None else out
+        (pU, k1), (pF, k2) = _ptr(U, None), _ptr(out, None)
+        if k1 != k2:
+            raise TypeError("all buffers must be on the same side (host or device)")
+        self._check(self._lib.stdg_spatial_operator(self._h, pU, pF, k1))
+        return out
+
+    def jv_fd_apply(self, U, F0, v, eps, out):
+        """One FD Jacobian-vector kernel launch on device tensors (as issued inside GMRES)."""
+        ptrs = [_ptr(x, None) for x in (U, F0, v, out)]
+        if any(k != DEVICE for _, k in ptrs):
+            raise TypeError("jv_fd_apply takes device tensors")
+        self._check(self._lib.stdg_jv_fd_apply(self._h, ptrs[0][0], ptrs[1][0], ptrs[2][0], float(eps), ptrs[3][0]))
+        return out
+
+    def profile_enable(self, on=True):
+        self._check(self._lib.stdg_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, reset=True):
+        p = stdg_profile()
+        self._check(self._lib.stdg_profile_read(self._h, ctypes.byref(p), 1 if reset else 0))
+        return {name: {"launches": p.launches[i], "ms": p.ms[i]} for i, name in enumerate(PROFILE_CLASSES)}
 
     def slab_norm(self, x):
         p, kind = _ptr(x, None)
