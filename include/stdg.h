@@ -170,6 +170,32 @@ stdg_status stdg_profile_enable(stdg_ctx* ctx, int on);
 /* Synchronises the context stream, returns the sums since the last reset. */
 stdg_status stdg_profile_read(stdg_ctx* ctx, stdg_profile* out, int reset);
 
+/* ||x||_2 of a device vector without allocating anything on the device.
+ *
+ * No counterpart in the paper: this is a service entry point for callers that
+ * cannot allocate device memory (stdg_create allocates the Krylov basis and
+ * scratch of a context), for instance a host whose device memory is held
+ * entirely by its own pool allocator, or a latency-critical loop that must not
+ * call cudaMalloc/cudaFree (cudaFree synchronises the device).  It computes
+ * the same value as stdg_slab_norm (FP64 squares, per-block partial sums,
+ * fixed-order final sum) for any length up to STDG_NORM_NOALLOC_MAX_LEN.
+ *   x            device pointer to len doubles (may be NULL when len == 0)
+ *   out          device pointer to one double, receives the norm
+ *   cuda_stream  cudaStream_t the two kernels are enqueued on (NULL = default)
+ * The per-block partial sums live in one static device array of 4096 doubles
+ * (32 KB) that every device which loads the library holds until exit.  It is
+ * shared by all calls on a device: calls that may overlap on the GPU (e.g. on
+ * two streams) race on it and must be ordered by the caller.  Every slot a
+ * call reads was written by the same call, so no clearing is needed.  The
+ * first call on a device, with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Returns STDG_ERR_INVALID_ARG for a NULL pointer or
+ * len > STDG_NORM_NOALLOC_MAX_LEN (nothing is launched), STDG_ERR_CUDA when the
+ * set-up or a launch fails, else STDG_OK once the work is enqueued.  Calls no
+ * allocating routine. */
+#define STDG_NORM_NOALLOC_MAX_LEN ((size_t)67108864) /* 4096 blocks x 16384 values */
+stdg_status stdg_slab_norm_noalloc(const double* x, size_t len, double* out, void* cuda_stream);
+
 const char* stdg_last_error(const stdg_ctx* ctx);
 const char* stdg_status_string(stdg_status st);
 /* Library version string. */

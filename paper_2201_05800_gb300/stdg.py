@@ -268,3 +268,21 @@ def version():
 
 def status_string(st):
     return load().stdg_status_string(st).decode()
+
+
+def slab_norm_noalloc(x, out, stream=None):
+    """stdg_slab_norm_noalloc: ||x||_2 of a device FP64 tensor into the one-element device
+    tensor ``out`` without any device allocation (for callers that cannot allocate; the
+    partial sums live in a static device array, see include/stdg.h)."""
+    lib = load()
+    fn = lib.stdg_slab_norm_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [_P, ctypes.c_size_t, _P, _P]
+    px, kx = _ptr(x, None)
+    po, ko = _ptr(out, None)
+    if kx != DEVICE or ko != DEVICE:
+        raise TypeError("slab_norm_noalloc takes device tensors")
+    st = fn(px, x.numel(), po, ctypes.c_void_p(stream) if stream is not None else None)
+    if st != 0:
+        raise StdgError(st, "stdg_slab_norm_noalloc")
+    return out
