@@ -329,6 +329,7 @@ def gpu_arm(args):
                            "frac_fp64_peak": r_flops / (r_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                            "hbm_gbs_algorithmic": (2 * dof + dof / s) * 8 / (r_ms * 1e-3) / 1e9}
         clocks = clk.summary()
+        u_fp64 = ctx.get_state()  # state after warm-up + timed slabs (FP64 path)
 
         # ---- end to end through the public API with host (pinned) buffers
         hin = torch.from_numpy(ctx.get_state()).pin_memory()
@@ -348,6 +349,10 @@ def gpu_arm(args):
         e2e_s = _max_over_ranks(time.perf_counter() - t0, ws)
         e2e_value = _sum_over_ranks(float(e2e_evals * dof), ws) / e2e_s / 1e9
         ctx.close()
+
+        # ---- the same slabs on the mixed-precision path (FP32 exact Jv and Krylov basis,
+        #      FP64 Newton residual and update): throughput and distance to the FP64 path
+        mixed = _mixed_path(stdg, desc, u0, args, stream, u_fp64, ws)
 
     lat_ms = sorted(1e3 * x for x in lat)
     cpu = None
@@ -382,12 +387,52 @@ def gpu_arm(args):
                 "roofline": roofline, "clocks": clocks,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hin.numel() * 8),
                         "d2h_bytes_per_step": int(hout.numel() * 8)},
-                "gpu_launches": launches, "cpu_baseline": cpu}
+                "gpu_launches": launches, "cpu_baseline": cpu, "mixed_fp32": mixed}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _mixed_path(stdg, desc, u0, args, stream, u_ref, ws):
+    """March the same warm-up + timed slabs with STDG_MIXED_FP32 (exact FP32 Jv); time the
+    timed ones with CUDA events and compare the final state with the FP64 path's."""
+    import ctypes
+
+    import numpy as np
+    import torch
+    dm = stdg.stdg_config_desc()
+    ctypes.memmove(ctypes.byref(dm), ctypes.byref(desc), ctypes.sizeof(desc))
+    dm.precision = stdg.MIXED_FP32
+    dm.jv_mode = stdg.JV_EXACT
+    ctx = stdg.Context(dm, stream.cuda_stream)
+    dof = ctx.slab_len
+    ctx.set_state(u0)
+    for _ in range(args.warmup):
+        ctx.advance_slab()
+    ctx.profile_enable(True)
+    ctx.profile_read(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stats = [ctx.advance_slab() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read(reset=True)
+    ms = _max_over_ranks(e0.elapsed_time(e1), ws)
+    u = ctx.get_state()
+    ctx.close()
+    evals = sum(st["residual_evals"] + st["jv_evals"] for st in stats)
+    return {"precision": "FP32 Jv (exact, forward mode) + FP32 Krylov basis, FP64 Newton residual/update",
+            "value": _sum_over_ranks(float(evals * dof), ws) / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "ms_per_step": ms / args.steps,
+            "slab_solves_per_s": _sum_over_ranks(float(args.steps), ws) / (ms * 1e-3),
+            "rel_l2_vs_fp64_path": float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref)),
+            "newton_its": [st["newton_its"] for st in stats], "gmres_its": [st["gmres_its"] for st in stats],
+            "kernel_time_ms": {k: v["ms"] for k, v in prof.items()},
+            "kernel_launches": {k: v["launches"] for k, v in prof.items()}}
 
 
 def _ncu_traffic():

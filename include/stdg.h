@@ -73,6 +73,12 @@ enum { STDG_FLUX_RUSANOV = 0 };             /* Eq. flux:llf; upwind for advectio
 enum { STDG_FP64 = 0, STDG_MIXED_FP32 = 1 };/* precision of Jv and the GMRES basis       */
 enum { STDG_JV_FD = 0, STDG_JV_EXACT = 1 }; /* finite-difference JFNK or forward mode    */
 enum { STDG_HOST = 0, STDG_DEVICE = 1 };
+/* GMRES preconditioning of J dU = -R.  STDG_PRECOND_TEMPORAL_MASS solves the
+ * left-scaled system (M_tau^-1 (x) I) J dU = -(M_tau^-1 (x) I) R: the rows of
+ * temporal node m are divided by the LGL weight omega_m (a diagonal scaling;
+ * the inner tolerance gmres_rtol then refers to the scaled residual).  The
+ * Newton test always uses the unscaled ||R||_2. */
+enum { STDG_PRECOND_NONE = 0, STDG_PRECOND_TEMPORAL_MASS = 1 };
 
 typedef struct {
   int dim;                  /* spatial dimension d, 1..3                                 */
@@ -94,6 +100,7 @@ typedef struct {
   double gmres_rtol;        /* inner tolerance eta (relative to ||R||)                   */
   int gmres_maxit;          /* total inner iterations per Newton step, >= 1              */
   size_t hbm_budget_bytes;  /* 0 = unlimited; else create fails with STDG_ERR_OOM above  */
+  int precond;              /* STDG_PRECOND_NONE | STDG_PRECOND_TEMPORAL_MASS (default)  */
 } stdg_config_desc;
 
 typedef struct {

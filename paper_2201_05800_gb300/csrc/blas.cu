@@ -29,37 +29,54 @@ __device__ __forceinline__ void block_store(const double (&acc)[K], double* out)
   }
 }
 
+// Per-thread arithmetic precision: FP32 data is combined in FP32 (an FP64
+// operation per element would make the FP32 passes FP64-pipe bound); FP64
+// data in FP64.  Cross-thread sums are always FP64.
+template <class TV> struct Compute { using type = double; };
+template <> struct Compute<float> { using type = float; };
+
 template <class TV, class TW, int K>
 __global__ void __launch_bounds__(kRedThreads) multidot_kernel(const TV* __restrict__ V, size_t ld,
                                                                const TW* __restrict__ w, size_t L,
                                                                double* __restrict__ partials) {
-  double acc[K];
+  using CT = typename Compute<TV>::type;
+  CT acc[K];
 #pragma unroll
-  for (int i = 0; i < K; ++i) acc[i] = 0.0;
+  for (int i = 0; i < K; ++i) acc[i] = CT(0);
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < L; idx += stride) {
-    const double wv = (double)w[idx];
+    const CT wv = (CT)w[idx];
 #pragma unroll
-    for (int i = 0; i < K; ++i) acc[i] = fma((double)V[(size_t)i * ld + idx], wv, acc[i]);
+    for (int i = 0; i < K; ++i) acc[i] = fma((CT)V[(size_t)i * ld + idx], wv, acc[i]);
   }
-  block_store<K>(acc, partials + (size_t)blockIdx.x * kPartialStride);
+  double accd[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) accd[i] = (double)acc[i];
+  block_store<K>(accd, partials + (size_t)blockIdx.x * kPartialStride);
 }
 
+// w -= sum_i c_i V_i; the sum is formed in the basis precision and added to w
+// in w's precision (FP32 basis into an FP64 w: one FP64 add per element).
 template <class TV, class TW>
 __global__ void __launch_bounds__(kRedThreads) update_kernel(TW* __restrict__ w, const TV* __restrict__ V, size_t ld,
                                                              int k, const __grid_constant__ Coefs c, size_t L) {
+  using CT = typename Compute<TV>::type;
+  using WT = typename Compute<TW>::type;
+  __shared__ CT cn[kMaxDots];  // -c in the compute precision, converted once per block
+  if (threadIdx.x < kMaxDots) cn[threadIdx.x] = threadIdx.x < k ? (CT)(-c.c[threadIdx.x]) : CT(0);
+  __syncthreads();
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < L; idx += stride) {
-    double x0 = (double)w[idx], x1 = 0.0, x2 = 0.0, x3 = 0.0;
+    CT x0 = CT(0), x1 = CT(0), x2 = CT(0), x3 = CT(0);
     int i = 0;
     for (; i + 4 <= k; i += 4) {
-      x0 = fma(-c.c[i], (double)V[(size_t)i * ld + idx], x0);
-      x1 = fma(-c.c[i + 1], (double)V[(size_t)(i + 1) * ld + idx], x1);
-      x2 = fma(-c.c[i + 2], (double)V[(size_t)(i + 2) * ld + idx], x2);
-      x3 = fma(-c.c[i + 3], (double)V[(size_t)(i + 3) * ld + idx], x3);
+      x0 = fma(cn[i], (CT)V[(size_t)i * ld + idx], x0);
+      x1 = fma(cn[i + 1], (CT)V[(size_t)(i + 1) * ld + idx], x1);
+      x2 = fma(cn[i + 2], (CT)V[(size_t)(i + 2) * ld + idx], x2);
+      x3 = fma(cn[i + 3], (CT)V[(size_t)(i + 3) * ld + idx], x3);
     }
-    for (; i < k; ++i) x0 = fma(-c.c[i], (double)V[(size_t)i * ld + idx], x0);
-    w[idx] = (TW)((x0 + x1) + (x2 + x3));
+    for (; i < k; ++i) x0 = fma(cn[i], (CT)V[(size_t)i * ld + idx], x0);
+    w[idx] = (TW)((WT)w[idx] + (WT)((x0 + x1) + (x2 + x3)));
   }
 }
 
@@ -86,6 +103,20 @@ __global__ void scale_add_kernel(TY* y, const TX* x, double a, const TX* z, doub
     double v = a * (double)x[idx];
     if (z) v = fma(b, (double)z[idx], v);
     y[idx] = (TY)v;
+  }
+}
+
+template <class T>
+__global__ void tnode_scale_add_kernel(T* y, const T* x, double a, const TimeWeights w, const T* z, double b,
+                                       long long nelem, int s, int blk) {
+  // y may alias x or z: no __restrict__ here
+  const size_t total = (size_t)nelem * s * blk;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+    const int m = (int)((idx / blk) % s);
+    double v = a * w.w[m] * (double)x[idx];
+    if (z) v = fma(b, (double)z[idx], v);
+    y[idx] = (T)v;
   }
 }
 
@@ -162,6 +193,13 @@ cudaError_t scale_add(TY* y, const TX* x, double a, const TX* z, double b, size_
 }
 
 template <class T>
+cudaError_t tnode_scale_add(T* y, const T* x, double a, const TimeWeights& w, const T* z, double b,
+                            long long nelem, int s, int blk, cudaStream_t st) {
+  tnode_scale_add_kernel<T><<<grid_for((size_t)nelem * s * blk), 256, 0, st>>>(y, x, a, w, z, b, nelem, s, blk);
+  return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t broadcast_slab(T* U, const T* u, long long nelem, int s, int blk, cudaStream_t st) {
   broadcast_kernel<T><<<grid_for((size_t)nelem * s * blk), 256, 0, st>>>(U, u, nelem, s, blk);
   return cudaGetLastError();
@@ -182,6 +220,10 @@ template cudaError_t scale_add<double, double>(double*, const double*, double, c
 template cudaError_t scale_add<double, float>(float*, const double*, double, const double*, double, size_t, cudaStream_t);
 template cudaError_t scale_add<float, float>(float*, const float*, double, const float*, double, size_t, cudaStream_t);
 template cudaError_t scale_add<float, double>(double*, const float*, double, const float*, double, size_t, cudaStream_t);
+template cudaError_t tnode_scale_add<double>(double*, const double*, double, const TimeWeights&, const double*, double,
+                                             long long, int, int, cudaStream_t);
+template cudaError_t tnode_scale_add<float>(float*, const float*, double, const TimeWeights&, const float*, double,
+                                            long long, int, int, cudaStream_t);
 template cudaError_t broadcast_slab<double>(double*, const double*, long long, int, int, cudaStream_t);
 template cudaError_t extract_last<double>(double*, const double*, long long, int, int, cudaStream_t);
 

@@ -41,6 +41,15 @@ cudaError_t reduce_partials(const double* partials, int nblk, int count, double*
 template <class TX, class TY>
 cudaError_t scale_add(TY* y, const TX* x, double a, const TX* z, double b, size_t L, cudaStream_t st);
 
+// Per temporal node weights of a slab, passed by value.
+struct TimeWeights {
+  double w[8];
+};
+// y[e][m][q] = a * w[m] * x[e][m][q] (+ b * z[e][m][q] if z); y may alias x or z
+template <class T>
+cudaError_t tnode_scale_add(T* y, const T* x, double a, const TimeWeights& w, const T* z, double b,
+                            long long nelem, int s, int per_node_block, cudaStream_t st);
+
 // U[e][m][:] = u[e][:] for all m (initial guess 1 (x) u^n)
 template <class T>
 cudaError_t broadcast_slab(T* U, const T* u, long long nelem, int s, int per_node_block, cudaStream_t st);

@@ -45,6 +45,8 @@ struct OpArgs {
   T eps;                   // FD step (kModeJvFD)
   T inv_eps;               // 1 / eps
   T vscale;                // v is read as vscale * v (kModeJvFD / kModeJvExact)
+  int lscale;              // Jv modes: rows of temporal node m divided by omega_m
+  T inv_omega[kMaxS];      // 1 / omega_m
   const T* U;              // slab, [e][m][node][c]
   const T* v;              // direction, same layout
   const T* F0;             // F(U), same layout (kModeJvFD)

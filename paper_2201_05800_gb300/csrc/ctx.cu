@@ -4,13 +4,14 @@
 // Slab solve (Sec. 6.3, Newton-type nonlinear solver with a Krylov linear
 // solver, as in the paper's 3D runs): U0 = 1 (x) u^n; while ||R(U)|| is above
 // max(rtol ||R(U0)||, atol): solve J(U) dU = -R(U) by restarted GMRES(m) with
-// classical Gram-Schmidt and one re-orthogonalisation pass (CGS2), Givens
-// rotations on the host, matrix-free J v by the space-time operator kernel;
-// U += dU.  Then u^{n+1} = U^s (Eq. un).
+// classical Gram-Schmidt and selective re-orthogonalisation, Givens rotations
+// on the host, matrix-free J v by the space-time operator kernel, optional left
+// scaling by M_tau^-1; U += dU.  Then u^{n+1} = U^s (Eq. un).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "blas.cuh"
@@ -40,7 +41,10 @@ struct stdg_ctx {
   OpArgs<double> a64;
   OpArgs<float> a32;
   int epb64[3] = {1, 1, 1};
+  int epb32[3] = {1, 1, 1};
   int nblk = 1;
+  // FP32 buffers of the mixed-precision Krylov solve (STDG_MIXED_FP32 only)
+  float *U32 = nullptr, *F032 = nullptr, *R32 = nullptr, *X32 = nullptr, *V32 = nullptr;
   std::vector<void*> allocs;
   size_t bytes = 0;
   double *U = nullptr, *R = nullptr, *F0 = nullptr, *delta = nullptr, *uprev = nullptr;
@@ -175,6 +179,7 @@ void fill_args(const stdg_ctx* c, OpArgs<T>& k) {
   k.gamma = (T)c->d.gamma;
   for (int a = 0; a < 3; ++a) k.adv[a] = (T)c->d.adv_vel[a];
   k.vscale = (T)1;
+  for (int m = 0; m < c->s; ++m) k.inv_omega[m] = (T)(1.0 / om[m]);
 }
 
 stdg_status validate(const stdg_config_desc* d, std::string* why) {
@@ -197,11 +202,13 @@ stdg_status validate(const stdg_config_desc* d, std::string* why) {
   if (d->newton_maxit < 1 || d->gmres_maxit < 1) return bad("maxit must be >= 1");
   if (d->gmres_m < 1 || d->gmres_m > kMaxGmresM) return bad("gmres_m must be 1..31");
   if (!(d->newton_rtol >= 0) || !(d->newton_atol >= 0) || !(d->gmres_rtol > 0)) return bad("bad tolerance");
+  if (d->precond != STDG_PRECOND_NONE && d->precond != STDG_PRECOND_TEMPORAL_MASS) return bad("unknown precond");
   return STDG_OK;
 }
 
-stdg_status alloc(stdg_ctx* c, double** p, size_t count) {
-  size_t b = count * sizeof(double);
+template <class T>
+stdg_status alloc(stdg_ctx* c, T** p, size_t count) {
+  size_t b = count * sizeof(T);
   if (c->d.hbm_budget_bytes && c->bytes + b > c->d.hbm_budget_bytes)
     return fail(c, STDG_ERR_OOM, "allocation exceeds hbm_budget_bytes");
   void* q = nullptr;
@@ -212,7 +219,7 @@ stdg_status alloc(stdg_ctx* c, double** p, size_t count) {
   }
   c->allocs.push_back(q);
   c->bytes += b;
-  *p = static_cast<double*>(q);
+  *p = static_cast<T*>(q);
   return STDG_OK;
 }
 
@@ -227,7 +234,7 @@ int choose_epb(const stdg_ctx* c, int mode, size_t tsize) {
   return epb;
 }
 
-// ---- operator launches (FP64)
+// ---- operator launches
 stdg_status op_residual(stdg_ctx* c, const double* U, const double* uprev, double* out, double* fout) {
   OpArgs<double> k = c->a64;
   k.epb = c->epb64[kModeResidual];
@@ -240,26 +247,66 @@ stdg_status op_residual(stdg_ctx* c, const double* U, const double* uprev, doubl
   return STDG_OK;
 }
 
-stdg_status op_jv(stdg_ctx* c, const double* U, const double* F0, const double* v, double vscale, double eps,
-                  double* out) {
-  const int mode = c->d.jv_mode == STDG_JV_EXACT ? kModeJvExact : kModeJvFD;
-  OpArgs<double> k = c->a64;
-  k.epb = c->epb64[mode];
+// Buffers and constants of one working precision of the Krylov solve: FP64
+// (plain path) or FP32 (STDG_MIXED_FP32, Newton stays FP64).
+template <class T>
+struct KView {
+  const OpArgs<T>* args;
+  const int* epb;
+  T* U;   // Newton iterate in T
+  T* F0;  // F(U) in T (FD Jv)
+  T* R;   // Newton residual in T
+  T* X;   // slab scratch in T
+  T* V;   // Krylov basis, gmres_m + 1 rows
+};
+
+KView<double> view(stdg_ctx* c, double*) { return {&c->a64, c->epb64, c->U, c->F0, c->R, c->X1, c->V}; }
+KView<float> view(stdg_ctx* c, float*) { return {&c->a32, c->epb32, c->U32, c->F032, c->R32, c->X32, c->V32}; }
+
+// F(U) only, in precision T (FD Jv base point of the mixed path)
+template <class T>
+stdg_status op_spatial(stdg_ctx* c, const KView<T>& kv, const T* U, T* fout) {
+  OpArgs<T> k = *kv.args;
+  k.epb = kv.epb[kModeResidual];
   k.U = U;
-  k.v = v;
-  k.F0 = F0;
-  k.vscale = vscale;
-  k.eps = eps;
-  k.inv_eps = eps > 0.0 ? 1.0 / eps : 0.0;
-  k.out = out;
-  Prof p(c, 1);
-  CK(c, launch_operator<double>(c->dim, c->d.equation, mode, k, c->st));
+  k.uprev = nullptr;
+  k.out = nullptr;
+  k.fout = fout;
+  Prof p(c, 0);
+  CK(c, launch_operator<T>(c->dim, c->d.equation, kModeResidual, k, c->st));
   return STDG_OK;
 }
 
+// lscale: rows of temporal node m divided by omega_m (the GMRES left scaling of
+// STDG_PRECOND_TEMPORAL_MASS); the public stdg_jv always returns J v unscaled.
+template <class T>
+stdg_status op_jv_t(stdg_ctx* c, const KView<T>& kv, const T* U, const T* F0, const T* v, double vscale,
+                    double eps, T* out, bool lscale) {
+  const int mode = c->d.jv_mode == STDG_JV_EXACT ? kModeJvExact : kModeJvFD;
+  OpArgs<T> k = *kv.args;
+  k.epb = kv.epb[mode];
+  k.U = U;
+  k.v = v;
+  k.F0 = F0;
+  k.vscale = (T)vscale;
+  k.eps = (T)eps;
+  k.inv_eps = eps > 0.0 ? (T)(1.0 / eps) : (T)0;
+  k.lscale = lscale ? 1 : 0;
+  k.out = out;
+  Prof p(c, 1);
+  CK(c, launch_operator<T>(c->dim, c->d.equation, mode, k, c->st));
+  return STDG_OK;
+}
+
+stdg_status op_jv(stdg_ctx* c, const double* U, const double* F0, const double* v, double vscale, double eps,
+                  double* out, bool lscale = false) {
+  return op_jv_t<double>(c, view(c, (double*)nullptr), U, F0, v, vscale, eps, out, lscale);
+}
+
 // ---- reductions
-stdg_status dots_to_small(stdg_ctx* c, const double* V, int k, const double* w, int small_off) {
-  PK(c, 2, (multidot<double, double>(V, c->slab_len, k, w, c->slab_len, c->partials, c->nblk, c->st)));
+template <class T>
+stdg_status dots_to_small(stdg_ctx* c, const T* V, int k, const T* w, int small_off) {
+  PK(c, 2, (multidot<T, T>(V, c->slab_len, k, w, c->slab_len, c->partials, c->nblk, c->st)));
   PK(c, 2, reduce_partials(c->partials, c->nblk, k, c->small + small_off, c->st));
   return STDG_OK;
 }
@@ -270,47 +317,75 @@ stdg_status fetch_small(stdg_ctx* c, int off, int count) {
   return STDG_OK;
 }
 
-stdg_status norm2(stdg_ctx* c, const double* x, size_t L, double* out) {
-  PK(c, 2, (multidot<double, double>(x, L, 1, x, L, c->partials, c->nblk, c->st)));
+template <class T>
+stdg_status norm2(stdg_ctx* c, const T* x, size_t L, double* out) {
+  PK(c, 2, (multidot<T, T>(x, L, 1, x, L, c->partials, c->nblk, c->st)));
   PK(c, 2, reduce_partials(c->partials, c->nblk, 1, c->small + 200, c->st));
   CKS(fetch_small(c, 200, 1));
   *out = std::sqrt(c->hpin[200]);
   return STDG_OK;
 }
 
-double fd_base_eps() { return std::sqrt(2.220446049250313e-16); }
+// delta as the T-typed input of a Jacobian-vector product (the FP32 copy lives in X)
+template <class T> const T* delta_in(stdg_ctx* c, T* X);
+template <> const double* delta_in<double>(stdg_ctx* c, double*) { return c->delta; }
+template <> const float* delta_in<float>(stdg_ctx*, float* X) { return X; }
 
-// ---- GMRES(m) for J(U) delta = -R, delta accumulated in c->delta.
+template <class T> double fd_base_eps();
+template <> double fd_base_eps<double>() { return std::sqrt(2.220446049250313e-16); }
+template <> double fd_base_eps<float>() { return std::sqrt(1.1920928955078125e-07); }
+
+// ---- GMRES(m) for J(U) delta = -R, delta (FP64) accumulated in c->delta.
 //
-// Arnoldi with classical Gram-Schmidt and the DGKS re-orthogonalisation test:
-// one fused pass gives p_i = V_i . w (i <= j) and |w|^2 (w is the row after
-// the basis); |w - V h|^2 = |w|^2 - |h|^2 (Pythagoras); a second projection is
-// made only when that norm fell below |w|/sqrt(2).  Basis rows are stored
-// unnormalised with scale factors sig_i (v_i = sig_i V_i), so no scaling pass
-// is needed; coefficients reach the update kernel by value.
-stdg_status gmres(stdg_ctx* c, double beta0, double eps_u, int* its_out, int* jv_out) {
+// Arnoldi with classical Gram-Schmidt and a selective re-orthogonalisation
+// test: one fused pass gives p_i = V_i . w (i <= j) and |w|^2 (w is the row
+// after the basis); |w - V h|^2 = |w|^2 - |h|^2 (Pythagoras); a second
+// projection is made only when that norm fell below |w|/10 (strong
+// cancellation; the classical DGKS bound 1/sqrt(2) fired in most steps of the
+// left-scaled system without changing iteration counts or the true residual).
+// Basis rows are stored unnormalised with scale factors sig_i
+// (v_i = sig_i V_i), so no scaling pass is needed; coefficients reach the
+// update kernel by value.  Hessenberg, Givens rotations and the triangular
+// solve are FP64 on the host in both precisions; the basis, the Jacobian-
+// vector products and the per-thread sums of the dot passes are in T.
+template <class T>
+stdg_status gmres(stdg_ctx* c, double eps_u, int* its_out, int* jv_out) {
+  const KView<T> kv = view(c, (T*)nullptr);
   const int m = c->d.gmres_m;
   const size_t L = c->slab_len;
-  const double tol = c->d.gmres_rtol * beta0;
+  const bool ls = c->d.precond == STDG_PRECOND_TEMPORAL_MASS;
+  const int blk = c->nd * c->r;
+  TimeWeights winv;  // left scaling of the rows of temporal node m (1 without preconditioning)
+  for (int q = 0; q < 8; ++q) winv.w[q] = (ls && q < c->s) ? 1.0 / (double)c->a64.omega[q] : 1.0;
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m), sig(m + 1);
   auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
-  auto Vrow = [&](int i) { return c->V + (size_t)i * L; };
+  auto Vrow = [&](int i) { return kv.V + (size_t)i * L; };
   CK(c, cudaMemsetAsync(c->delta, 0, L * sizeof(double), c->st));
+  // the Newton residual in T (a cast for the mixed path), then b = -(M^-1 (x) I) R (or -R)
+  if (!std::is_same<T, double>::value)
+    PK(c, 2, (scale_add<double, T>(kv.R, c->R, 1.0, nullptr, 0.0, L, c->st)));
+  PK(c, 2, (tnode_scale_add<T>(Vrow(0), kv.R, 1.0, winv, nullptr, 0.0, c->nelem, c->s, blk, c->st)));
+  double beta0;
+  CKS(norm2<T>(c, Vrow(0), L, &beta0));
+  const double tol = c->d.gmres_rtol * beta0;
   int its = 0, jvs = 0;
   bool first = true;
-  while (its < c->d.gmres_maxit) {
+  while (its < c->d.gmres_maxit && beta0 > 0.0) {
     double beta;
     if (first) {
-      PK(c, 2, (scale_add<double, double>(Vrow(0), c->R, 1.0, nullptr, 0.0, L, c->st)));
       beta = beta0;
-      sig[0] = -1.0 / beta0;  // v_0 = -R / |R|
+      sig[0] = -1.0 / beta0;  // v_0 = b / |b|, V_0 holds -b
     } else {
+      // restart: V_0 = -(b - J delta) with delta cast to T
       double nd;
-      CKS(norm2(c, c->delta, L, &nd));
-      CKS(op_jv(c, c->U, c->F0, c->delta, 1.0, eps_u / (nd > 0 ? nd : 1.0), Vrow(0)));
+      CKS(norm2<double>(c, c->delta, L, &nd));
+      if (!std::is_same<T, double>::value)
+        PK(c, 2, (scale_add<double, T>(kv.X, c->delta, 1.0, nullptr, 0.0, L, c->st)));
+      const T* dT = delta_in<T>(c, kv.X);
+      CKS(op_jv_t<T>(c, kv, kv.U, kv.F0, dT, 1.0, eps_u / (nd > 0 ? nd : 1.0), Vrow(0), ls));
       ++jvs;
-      PK(c, 2, (scale_add<double, double>(Vrow(0), c->R, -1.0, Vrow(0), -1.0, L, c->st)));
-      CKS(norm2(c, Vrow(0), L, &beta));
+      PK(c, 2, (tnode_scale_add<T>(Vrow(0), kv.R, -1.0, winv, Vrow(0), -1.0, c->nelem, c->s, blk, c->st)));
+      CKS(norm2<T>(c, Vrow(0), L, &beta));
       if (!(beta > tol)) break;
       sig[0] = 1.0 / beta;
     }
@@ -320,11 +395,11 @@ stdg_status gmres(stdg_ctx* c, double beta0, double eps_u, int* its_out, int* jv
     int kdim = 0;
     bool done = false;
     for (int j = 0; j < m && its < c->d.gmres_maxit; ++j) {
-      double* w = Vrow(j + 1);
-      CKS(op_jv(c, c->U, c->F0, Vrow(j), sig[j], eps_u, w));
+      T* w = Vrow(j + 1);
+      CKS(op_jv_t<T>(c, kv, kv.U, kv.F0, Vrow(j), sig[j], eps_u, w, ls));
       ++jvs;
       // p_i = V_i . w (i <= j) and |w|^2 in one pass over rows 0..j+1
-      CKS(dots_to_small(c, c->V, j + 2, w, 0));
+      CKS(dots_to_small<T>(c, kv.V, j + 2, w, 0));
       CKS(fetch_small(c, 0, j + 2));
       double w2 = c->hpin[j + 1], h2 = 0.0;
       Coefs cf;
@@ -333,11 +408,11 @@ stdg_status gmres(stdg_ctx* c, double beta0, double eps_u, int* its_out, int* jv
         h2 += Hij(i, j) * Hij(i, j);
         cf.c[i] = sig[i] * Hij(i, j);
       }
-      PK(c, 2, (update<double, double>(w, c->V, L, j + 1, cf, L, c->st)));
+      PK(c, 2, (update<T, T>(w, kv.V, L, j + 1, cf, L, c->st)));
       double r2 = w2 - h2;
-      if (!(r2 > 0.5 * w2)) {
-        // DGKS: severe cancellation, project once more and take the norm directly
-        CKS(dots_to_small(c, c->V, j + 2, w, 0));
+      if (!(r2 > 0.01 * w2)) {
+        // strong cancellation: project once more and take the norm directly
+        CKS(dots_to_small<T>(c, kv.V, j + 2, w, 0));
         CKS(fetch_small(c, 0, j + 2));
         double e2 = 0.0;
         for (int i = 0; i <= j; ++i) {
@@ -346,7 +421,7 @@ stdg_status gmres(stdg_ctx* c, double beta0, double eps_u, int* its_out, int* jv
           e2 += hi * hi;
           cf.c[i] = sig[i] * hi;
         }
-        PK(c, 2, (update<double, double>(w, c->V, L, j + 1, cf, L, c->st)));
+        PK(c, 2, (update<T, T>(w, kv.V, L, j + 1, cf, L, c->st)));
         r2 = c->hpin[j + 1] - e2;
       }
       if (!std::isfinite(r2) || !std::isfinite(w2)) return fail(c, STDG_ERR_NAN, "GMRES: non-finite Krylov vector");
@@ -381,7 +456,7 @@ stdg_status gmres(stdg_ctx* c, double beta0, double eps_u, int* its_out, int* jv
     if (kdim > 0) {
       Coefs cf;
       for (int i = 0; i < kdim; ++i) cf.c[i] = -y[i] * sig[i];
-      PK(c, 2, (update<double, double>(c->delta, c->V, L, kdim, cf, L, c->st)));
+      PK(c, 2, (update<T, double>(c->delta, kv.V, L, kdim, cf, L, c->st)));
     }
     if (done) break;
   }
@@ -420,6 +495,7 @@ void stdg_config_default(stdg_config_desc* d) {
   d->gmres_rtol = 1e-3;
   d->gmres_maxit = 300;
   d->hbm_budget_bytes = 0;
+  d->precond = STDG_PRECOND_TEMPORAL_MASS;
 }
 
 stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ctx** out) {
@@ -428,7 +504,7 @@ stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ct
   if (!desc) return STDG_ERR_INVALID_ARG;
   std::string why;
   if (validate(desc, &why) != STDG_OK) return STDG_ERR_INVALID_ARG;
-  if (desc->precision == STDG_MIXED_FP32) return STDG_ERR_UNSUPPORTED;
+  const bool mixed = desc->precision == STDG_MIXED_FP32;
   stdg_ctx* c = new stdg_ctx();
   c->d = *desc;
   c->st = static_cast<cudaStream_t>(cuda_stream);
@@ -456,6 +532,7 @@ stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ct
   fill_args(c, c->a32);
   for (int mode = 0; mode < 3; ++mode) {
     c->epb64[mode] = choose_epb(c, mode, sizeof(double));
+    c->epb32[mode] = choose_epb(c, mode, sizeof(float));
     if (operator_smem_bytes(c->dim, c->r, sizeof(double), mode, c->n, c->s, c->epb64[mode]) > kSmemLimit) {
       delete c;
       return STDG_ERR_UNSUPPORTED;
@@ -463,11 +540,14 @@ stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ct
   }
   c->nblk = 4 * c->sms;
   const size_t L = c->slab_len, S = c->state_len;
+  const size_t nbasis = L * (size_t)(desc->gmres_m + 1);
   stdg_status st = STDG_OK;
   if ((st = alloc(c, &c->U, L)) || (st = alloc(c, &c->R, L)) || (st = alloc(c, &c->F0, L)) ||
       (st = alloc(c, &c->delta, L)) || (st = alloc(c, &c->X1, L)) || (st = alloc(c, &c->X2, L)) ||
       (st = alloc(c, &c->uprev, S)) || (st = alloc(c, &c->Xs, S)) ||
-      (st = alloc(c, &c->V, L * (size_t)(desc->gmres_m + 1))) ||
+      (!mixed && (st = alloc(c, &c->V, nbasis))) ||
+      (mixed && ((st = alloc(c, &c->U32, L)) || (st = alloc(c, &c->F032, L)) || (st = alloc(c, &c->R32, L)) ||
+                 (st = alloc(c, &c->X32, L)) || (st = alloc(c, &c->V32, nbasis)))) ||
       (st = alloc(c, &c->partials, (size_t)c->nblk * kPartialStride)) || (st = alloc(c, &c->small, kSmall))) {
     stdg_destroy(c);
     return st;
@@ -593,9 +673,9 @@ stdg_status stdg_jv(stdg_ctx* c, const double* U, const double* uprev, const dou
   double eps = 0.0;
   if (c->d.jv_mode == STDG_JV_FD) {
     double nu, nv;
-    CKS(norm2(c, dU, c->slab_len, &nu));
-    CKS(norm2(c, dv, c->slab_len, &nv));
-    eps = fd_base_eps() * (1.0 + nu) / (nv > 0 ? nv : 1.0);
+    CKS(norm2<double>(c, dU, c->slab_len, &nu));
+    CKS(norm2<double>(c, dv, c->slab_len, &nv));
+    eps = fd_base_eps<double>() * (1.0 + nu) / (nv > 0 ? nv : 1.0);
     CKS(op_residual(c, dU, c->uprev, nullptr, c->F0));
   }
   CKS(op_jv(c, dU, c->F0, dv, 1.0, eps, dout));
@@ -614,7 +694,7 @@ stdg_status stdg_slab_norm(stdg_ctx* c, const double* x, int kind, double* out) 
     CK(c, cudaMemcpyAsync(c->X1, x, c->slab_len * sizeof(double), cudaMemcpyHostToDevice, c->st));
     dx = c->X1;
   }
-  return norm2(c, dx, c->slab_len, out);
+  return norm2<double>(c, dx, c->slab_len, out);
 }
 
 stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
@@ -628,9 +708,10 @@ stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
   CKS(op_residual(c, c->U, c->uprev, c->R, c->F0));
   ++S.residual_evals;
   double res;
-  CKS(norm2(c, c->R, L, &res));
+  CKS(norm2<double>(c, c->R, L, &res));
   S.res0 = res;
   const double target = std::fmax(c->d.newton_rtol * res, c->d.newton_atol);
+  const bool mixed = c->d.precision == STDG_MIXED_FP32;
   stdg_status status = STDG_OK;
   while (true) {
     if (!std::isfinite(res)) {
@@ -643,16 +724,23 @@ stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
       break;
     }
     double nu;
-    CKS(norm2(c, c->U, L, &nu));
-    const double eps_u = fd_base_eps() * (1.0 + nu);
+    CKS(norm2<double>(c, c->U, L, &nu));
     int its = 0, jvs = 0;
-    CKS(gmres(c, res, eps_u, &its, &jvs));
+    if (mixed) {
+      // inner solve in FP32 around the FP32 copy of the Newton iterate; the
+      // FP64 residual below refines (iterative refinement)
+      PK(c, 2, (scale_add<double, float>(c->U32, c->U, 1.0, nullptr, 0.0, L, c->st)));
+      if (c->d.jv_mode == STDG_JV_FD) CKS(op_spatial<float>(c, view(c, (float*)nullptr), c->U32, c->F032));
+      CKS(gmres<float>(c, fd_base_eps<float>() * (1.0 + nu), &its, &jvs));
+    } else {
+      CKS(gmres<double>(c, fd_base_eps<double>() * (1.0 + nu), &its, &jvs));
+    }
     S.gmres_its += its;
     S.jv_evals += jvs;
     PK(c, 2, (scale_add<double, double>(c->U, c->U, 1.0, c->delta, 1.0, L, c->st)));
     CKS(op_residual(c, c->U, c->uprev, c->R, c->F0));
     ++S.residual_evals;
-    CKS(norm2(c, c->R, L, &res));
+    CKS(norm2<double>(c, c->R, L, &res));
     ++S.newton_its;
   }
   S.res_final = res;

@@ -232,13 +232,18 @@ __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant_
           if (FIXED || j < s) lin += sC[j * kMaxS + m] * tile[((size_t)(el * s + j) * R + c) * ndp + node];
         if (m == s - 1) lin -= tile[((size_t)(el * s + m) * R + c) * ndp + node];
         if (MODE == kModeResidual) {
-          if (m == 0) lin += k.uprev[(size_t)(e0 + el) * nd * R + (size_t)node * R + c];
-          if (k.out) k.out[g] = lin + hw * val(Fv);
+          // u_prev is only read when R is written (F-only launches pass no u_prev)
+          if (k.out) {
+            if (m == 0) lin += k.uprev[(size_t)(e0 + el) * nd * R + (size_t)node * R + c];
+            k.out[g] = lin + hw * val(Fv);
+          }
           if (k.fout) k.fout[g] = val(Fv);
         } else if (MODE == kModeJvFD) {
-          k.out[g] = lin + hw * ((val(Fv) - k.F0[g]) * k.inv_eps);
+          const T dF = (val(Fv) - k.F0[g]) * k.inv_eps;
+          k.out[g] = k.lscale ? fma(k.inv_omega[m], lin, k.half_dt * dF) : fma(hw, dF, lin);
         } else {
-          k.out[g] = lin + hw * tangent(Fv);
+          const T dF = tangent(Fv);
+          k.out[g] = k.lscale ? fma(k.inv_omega[m], lin, k.half_dt * dF) : fma(hw, dF, lin);
         }
       }
     }

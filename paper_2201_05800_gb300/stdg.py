@@ -18,6 +18,7 @@ FLUX_RUSANOV = 0
 FP64, MIXED_FP32 = 0, 1
 JV_FD, JV_EXACT = 0, 1
 HOST, DEVICE = 0, 1
+PRECOND_NONE, PRECOND_TEMPORAL_MASS = 0, 1
 
 STATUS = {0: "STDG_OK", 1: "STDG_ERR_INVALID_ARG", 2: "STDG_ERR_OOM", 3: "STDG_ERR_CUDA",
           4: "STDG_ERR_NOT_CONVERGED", 5: "STDG_ERR_GMRES_BREAKDOWN", 6: "STDG_ERR_NAN",
@@ -33,7 +34,7 @@ class stdg_config_desc(ctypes.Structure):
                 ("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double),
                 ("newton_maxit", ctypes.c_int), ("gmres_m", ctypes.c_int),
                 ("gmres_rtol", ctypes.c_double), ("gmres_maxit", ctypes.c_int),
-                ("hbm_budget_bytes", ctypes.c_size_t)]
+                ("hbm_budget_bytes", ctypes.c_size_t), ("precond", ctypes.c_int)]
 
 
 class stdg_slab_stats(ctypes.Structure):

@@ -48,9 +48,10 @@ def test_config1_advection_100_slabs(S):
     assert st["newton_its"] >= 1 and st["gmres_its"] >= 1
 
 
-@pytest.mark.parametrize("jv", ["fd", "exact"])
-def test_vortex_slab_matches_oracle(S, jv):
-    """2D Euler vortex on [0,10]^2, 8x8 quads, N = 4, s = 4, CFL 0.5: one slab."""
+@pytest.mark.parametrize("jv,precond", [("fd", 1), ("exact", 1), ("fd", 0)])
+def test_vortex_slab_matches_oracle(S, jv, precond):
+    """2D Euler vortex on [0,10]^2, 8x8 quads, N = 4, s = 4, CFL 0.5: one slab (with and
+    without the left temporal-mass scaling of GMRES)."""
     prob = Problem(dim=2, cells=(8, 8), N=4, s=4, eq="euler", dt=1.0, lo=(0.0, 0.0), hi=(10.0, 10.0))
     X = prob.grid.coordinates()
     u0 = inputs.isentropic_vortex(X[0], X[1], center=(5.0, 5.0))
@@ -58,7 +59,7 @@ def test_vortex_slab_matches_oracle(S, jv):
     U_or = ost.solve_slab_newton_gmres("stdg", prob.F, u0, prob.dt, prob.s, rtol=1e-14, atol=1e-13,
                                        gmres_tol=1e-11, gmres_m=40)
     mode = S.JV_FD if jv == "fd" else S.JV_EXACT
-    with S.Context(prob.config(jv_mode=mode, **TIGHT)) as ctx:
+    with S.Context(prob.config(jv_mode=mode, precond=precond, **TIGHT)) as ctx:
         ctx.set_state(np.ascontiguousarray(u0).ravel())
         st = ctx.advance_slab()
         U = prob.from_ext(ctx.get_slab())
@@ -123,3 +124,44 @@ def test_failure_statuses_from_host_inputs(S):
     with pytest.raises(S.StdgError) as e:
         S.Context(prob.config(hbm_budget_bytes=1024))
     assert e.value.status == 2  # STDG_ERR_OOM
+
+
+@pytest.mark.parametrize("jv", ["fd", "exact"])
+def test_mixed_precision_refines_to_fp64_solution(S, jv):
+    """STDG_MIXED_FP32: FP32 Jacobian-vector products and Krylov basis inside FP64 Newton.
+    Iterated to FP64 tolerances the FP64 residual refines the solution to the oracle's
+    FP64 solution (1e-11); at the workload tolerances (rtol 1e-10, eta 1e-3) it stays
+    within the stated 1e-8 of it."""
+    prob = Problem(dim=2, cells=(8, 8), N=4, s=4, eq="euler", dt=1.0, lo=(0.0, 0.0), hi=(10.0, 10.0))
+    X = prob.grid.coordinates()
+    u0 = inputs.isentropic_vortex(X[0], X[1], center=(5.0, 5.0))
+    prob.dt = _cfl_dt(prob, u0)
+    U_or = ost.solve_slab_newton_gmres("stdg", prob.F, u0, prob.dt, prob.s, rtol=1e-14, atol=1e-13,
+                                       gmres_tol=1e-11, gmres_m=40)
+    mode = S.JV_FD if jv == "fd" else S.JV_EXACT
+    tight = dict(TIGHT, gmres_rtol=1e-4, newton_maxit=30)
+    with S.Context(prob.config(jv_mode=mode, precision=S.MIXED_FP32, **tight)) as ctx:
+        ctx.set_state(np.ascontiguousarray(u0).ravel())
+        st = ctx.advance_slab()
+        U = prob.from_ext(ctx.get_slab())
+    assert rel_lgl(prob, U, U_or) <= 1e-11, (rel_lgl(prob, U, U_or), st)
+    with S.Context(prob.config(jv_mode=mode, precision=S.MIXED_FP32, newton_rtol=1e-10,
+                               gmres_rtol=1e-3)) as ctx:
+        ctx.set_state(np.ascontiguousarray(u0).ravel())
+        ctx.advance_slab()
+        U = prob.from_ext(ctx.get_slab())
+    assert rel_lgl(prob, U, U_or) <= 1e-8, rel_lgl(prob, U, U_or)
+
+
+def test_mixed_precision_density_wave_3d(S):
+    prob = Problem(dim=3, cells=(3, 3, 3), N=3, s=3, eq="euler", dt=0.01)
+    u0 = inputs.density_wave(*prob.grid.coordinates())
+    prob.dt = _cfl_dt(prob, u0)
+    U_or = ost.solve_slab_newton_gmres("stdg", prob.F, u0, prob.dt, prob.s, rtol=1e-14, atol=1e-13,
+                                       gmres_tol=1e-11, gmres_m=40)
+    with S.Context(prob.config(precision=S.MIXED_FP32, jv_mode=S.JV_EXACT,
+                               **dict(TIGHT, gmres_rtol=1e-4, newton_maxit=30))) as ctx:
+        ctx.set_state(np.ascontiguousarray(u0).ravel())
+        ctx.advance_slab()
+        U = prob.from_ext(ctx.get_slab())
+    assert rel_lgl(prob, U, U_or) <= 1e-11, rel_lgl(prob, U, U_or)
