@@ -7,6 +7,7 @@
 // classical Gram-Schmidt and selective re-orthogonalisation, Givens rotations
 // on the host, matrix-free J v by the space-time operator kernel, optional left
 // scaling by M_tau^-1; U += dU.  Then u^{n+1} = U^s (Eq. un).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -223,15 +224,33 @@ stdg_status alloc(stdg_ctx* c, T** p, size_t count) {
   return STDG_OK;
 }
 
+// Elements per CTA of the operator kernel.  The kernel is throughput bound per
+// SM, so its time follows the most loaded SM: ceil(blocks / SMs) * epb
+// elements.  Score = load balance x active lanes x a small bonus for faces
+// shared inside a CTA; CTAs are limited by shared memory (228 KB per SM,
+// 1 KB reserved per CTA), threads (2048 per SM) and 32 CTAs per SM.
 int choose_epb(const stdg_ctx* c, int mode, size_t tsize) {
-  int epb = 256 / c->nd;
-  if (epb < 1) epb = 1;
-  // keep at least ~2 CTAs per SM when the grid allows it
-  long long want = (c->nelem + 2LL * c->sms - 1) / (2LL * c->sms);
-  if (want < 1) want = 1;
-  if (epb > want) epb = (int)want;
-  while (epb > 1 && operator_smem_bytes(c->dim, c->r, tsize, mode, c->n, c->s, epb) > kSmemLimit) --epb;
-  return epb;
+  int best = 1;
+  double best_score = -1.0;
+  const int max_epb = std::max(1, 256 / c->nd);
+  for (int epb = 1; epb <= max_epb && epb <= c->nelem; ++epb) {
+    const size_t smem = operator_smem_bytes(c->dim, c->r, tsize, mode, c->n, c->s, epb);
+    if (smem > kSmemLimit) break;
+    int threads = std::min(256, epb * c->nd);
+    threads = (threads + 31) / 32 * 32;
+    const int bps = std::min({(int)(233472 / (smem + 1024)), 2048 / threads, 32});
+    if (bps < 1) break;
+    const long long nblocks = (c->nelem + epb - 1) / epb;
+    const long long per_sm = (nblocks + c->sms - 1) / c->sms;
+    const double balance = ((double)c->nelem / c->sms) / (double)(per_sm * epb);
+    const double lanes = (double)std::min(epb * c->nd, 256) / threads;
+    const double score = balance * lanes * (1.0 + 0.1 * (epb - 1) / epb);
+    if (score > best_score + 1e-9) {
+      best_score = score;
+      best = epb;
+    }
+  }
+  return best;
 }
 
 // ---- operator launches

@@ -1,25 +1,32 @@
 // Fused space-time DG-SEM operator: residual R(U), or J(U) v, of one time slab.
 //
-// One CTA owns `epb` consecutive elements (all s temporal nodes of each).  The
-// element tiles are staged in shared memory (component-planar, padded to an
-// odd node stride), then for every temporal node m:
+// One CTA owns `epb` consecutive elements and walks the s temporal nodes of
+// their slab.  For every temporal node m:
+//   0. stage the element tiles of node m in shared memory (coalesced loads,
+//      component-planar, node stride padded to an odd count): U (residual),
+//      U + eps v (finite-difference Jv) or U and v (exact Jv)
 //   1. thread per node: f_a(u) and the wave speed |v_a| + c for all
 //      directions a (one reciprocal of rho, one pressure, one sound speed)
 //   2. thread per node: volume term  -sum_a (2/h_a) (D f_a)      -> smem acc
-//   3. thread per face point, one direction a at a time: Rusanov flux with
-//      the neighbour trace (read from global memory / L2; its flux and wave
-//      speed share one reciprocal and one pressure) and the strong-form face
-//      correction -(2/h_a)(1/w_end)(H.n - f_a(u).n) added to acc
+//   3. thread per face point, one direction a at a time: Rusanov flux and the
+//      strong-form face correction -(2/h_a)(1/w_end)(H.n - f_a(u).n).  A face
+//      between two elements of the CTA is computed once and applied to both
+//      sides from shared memory; for the others the neighbour trace is read
+//      from global memory (L2) and its flux and wave speed evaluated.
 //   4. thread per output value (coalesced): temporal coupling
 //        R_m = sum_j omega_j Dtau[j][m] U_j + [m=0] u_prev - [m=s-1] U_s
 //              + dt/2 omega_m F_m
-//      (Eq. DG_in_time moved to one side so that dR/dU is Eq. Jacobian_ST).
+//      (Eq. DG_in_time moved to one side so that dR/dU is Eq. Jacobian_ST),
+//      with U_j (or v_j) read from global memory (L2).
 // Strong form of the spatial operator (Sec. 3.1 with the SBP property of
 // Eq. SBP): F_I = -sum_a (2/h_a) [ sum_j D[i_a][j] f_a(u_(I,i_a->j))
 //      + (1/w_N) [i_a = N] (H_a^+ - f_a(u_I)) - (1/w_0) [i_a = 0] (H_a^- - f_a(u_I)) ].
-// The kernel is FP64-pipe bound in FP64 (ncu), so every FP64 operation it
-// can avoid is avoided: 2/h_a is folded into D, 1/eps is a multiplication,
-// wave speeds are computed once per node.
+// Only one temporal node is staged at a time so that many elements are
+// resident per SM (the whole bench grid fits one wave).  The kernel is
+// FP64-pipe bound in FP64 (ncu), so FP64 operations are avoided where
+// possible: 2/h_a is folded into D, 1/eps and the GMRES left scaling 1/omega_m
+// into the output factors, wave speeds are computed once per node, shared
+// faces once per face.
 #pragma once
 
 #include <type_traits>
@@ -35,6 +42,12 @@ __device__ __forceinline__ auto eval_state(T u, T v, T eps) {
   else if constexpr (MODE == kModeJvFD) return u + eps * v;
   else return u;
 }
+// State of a staged tile node (the FD tile already holds U + eps v).
+template <int MODE, class T>
+__device__ __forceinline__ auto tile_state(T u, T v) {
+  if constexpr (MODE == kModeJvExact) return Dual<T>{u, v};
+  else return u;
+}
 template <class T> __device__ __forceinline__ T tangent(Dual<T> x) { return x.d; }
 template <class T> __device__ __forceinline__ T tangent(T x) { return T(0); }
 
@@ -43,16 +56,17 @@ __host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b *
 // Shared-memory footprint (bytes) of one CTA.
 template <int DIM, int R, class T, int MODE>
 __host__ __device__ inline size_t op_smem_bytes(int n, int s, int epb) {
+  (void)s;
   int nd = 1;
   for (int a = 0; a < DIM; ++a) nd *= n;
   int ndp = nd | 1;
   size_t vbytes = (MODE == kModeJvExact) ? 2 * sizeof(T) : sizeof(T);
-  size_t b = (size_t)epb * s * R * ndp * sizeof(T);            // U tile
-  if (MODE != kModeResidual) b += (size_t)epb * s * R * ndp * sizeof(T);  // v tile
-  b += (size_t)epb * DIM * R * ndp * vbytes;                     // fluxes
-  b += (size_t)epb * R * ndp * vbytes;                           // accumulators
-  b += (size_t)epb * DIM * ndp * vbytes;                         // wave speeds
-  b += (3 * kMaxN * kMaxN + kMaxS * kMaxS) * sizeof(T);          // scaled D per direction, C
+  size_t b = (size_t)epb * R * ndp * sizeof(T);                     // state tile of node m
+  if (MODE == kModeJvExact) b += (size_t)epb * R * ndp * sizeof(T);  // direction tile of node m
+  b += (size_t)epb * DIM * R * ndp * vbytes;                        // fluxes
+  b += (size_t)epb * R * ndp * vbytes;                              // accumulators
+  b += (size_t)epb * DIM * ndp * vbytes;                            // wave speeds
+  b += (3 * kMaxN * kMaxN + kMaxS * kMaxS) * sizeof(T);             // scaled D per direction, C
   return b;
 }
 
@@ -75,48 +89,51 @@ __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant_
   const int tid = threadIdx.x, nth = blockDim.x;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* su = reinterpret_cast<T*>(smem_raw);                       // [epb][s][R][ndp]
-  T* sv = su + (size_t)epb * s * R * ndp;                        // [epb][s][R][ndp] (Jv modes)
-  V* sf = reinterpret_cast<V*>(MODE == kModeResidual ? sv : sv + (size_t)epb * s * R * ndp);  // [epb][DIM][R][ndp]
-  V* sr = sf + (size_t)epb * DIM * R * ndp;                      // [epb][R][ndp]
-  V* sl = sr + (size_t)epb * R * ndp;                            // [epb][DIM][ndp] wave speeds
-  T* sD = reinterpret_cast<T*>(sl + (size_t)epb * DIM * ndp);    // [3][kMaxN][kMaxN]  (2/h_a) D
-  T* sC = sD + 3 * kMaxN * kMaxN;                                // [kMaxS][kMaxS]  C
+  T* su = reinterpret_cast<T*>(smem_raw);                             // [epb][R][ndp] state of node m
+  T* sv = su + (size_t)epb * R * ndp;                                  // [epb][R][ndp] direction (exact)
+  V* sf = reinterpret_cast<V*>(MODE == kModeJvExact ? sv + (size_t)epb * R * ndp : sv);  // [epb][DIM][R][ndp]
+  V* sr = sf + (size_t)epb * DIM * R * ndp;                            // [epb][R][ndp]
+  V* sl = sr + (size_t)epb * R * ndp;                                  // [epb][DIM][ndp] wave speeds
+  T* sD = reinterpret_cast<T*>(sl + (size_t)epb * DIM * ndp);          // [3][kMaxN][kMaxN]  (2/h_a) D
+  T* sC = sD + 3 * kMaxN * kMaxN;                                      // [kMaxS][kMaxS]  C
   for (int i = tid; i < 3 * kMaxN * kMaxN; i += nth) {
     const int a = i / (kMaxN * kMaxN), q = i % (kMaxN * kMaxN);
     sD[i] = k.ginv[a] * k.D[q / kMaxN][q % kMaxN];
   }
   for (int i = tid; i < kMaxS * kMaxS; i += nth) sC[i] = k.C[i / kMaxS][i % kMaxS];
 
-  const size_t slab_elem = (size_t)s * nd * R;  // values of one element's slab
-  // ---- stage the element tiles (coalesced global reads, planar smem writes)
-  {
-    const size_t total = (size_t)nel * slab_elem;
-    const T* gU = k.U + (size_t)e0 * slab_elem;
-    const T* gv = (MODE != kModeResidual) ? k.v + (size_t)e0 * slab_elem : nullptr;
-    for (size_t idx = tid; idx < total; idx += nth) {
-      int c = (int)(idx % R);
-      size_t t = idx / R;
-      int node = (int)(t % nd);
-      t /= nd;  // = el * s + m
-      size_t so = (t * R + c) * ndp + node;
-      su[so] = gU[idx];
-      if (MODE != kModeResidual) sv[so] = k.vscale * gv[idx];
-    }
-  }
-  __syncthreads();
-
-  int strides[3] = {1, n, n * n};
+  const size_t tnode = (size_t)nd * R;  // values of one element at one temporal node
+  const int strides[3] = {1, n, n * n};
+  // the tile the temporal coupling acts on: U for the residual, v for J v
+  const T* gtile = (MODE == kModeResidual) ? k.U : k.v;
 
   for (int m = 0; m < s; ++m) {
-    // ---- 1. fluxes and wave speeds at every node of the temporal node m
+    // ---- 0. stage node m of the CTA's elements (coalesced global reads)
+    for (int idx = tid; idx < nel * (int)tnode; idx += nth) {
+      const int c = idx % R;
+      const int r2 = idx / R;
+      const int node = r2 % nd;
+      const int el = r2 / nd;
+      const size_t g = ((size_t)(e0 + el) * s + m) * tnode + (size_t)node * R + c;
+      const size_t so = ((size_t)el * R + c) * ndp + node;
+      if constexpr (MODE == kModeJvFD) {
+        su[so] = k.U[g] + k.eps * (k.vscale * k.v[g]);
+      } else if constexpr (MODE == kModeJvExact) {
+        su[so] = k.U[g];
+        sv[so] = k.vscale * k.v[g];
+      } else {
+        su[so] = k.U[g];
+      }
+    }
+    __syncthreads();
+    // ---- 1. fluxes and wave speeds at every node
     for (int t = tid; t < nel * nd; t += nth) {
-      int el = t / nd, node = t - el * nd;
-      size_t so = ((size_t)(el * s + m) * R) * ndp + node;
+      const int el = t / nd, node = t - el * nd;
+      const size_t so = ((size_t)el * R) * ndp + node;
       V u[R];
 #pragma unroll
       for (int c = 0; c < R; ++c)
-        u[c] = eval_state<MODE>(su[so + c * ndp], MODE == kModeResidual ? T(0) : sv[so + c * ndp], k.eps);
+        u[c] = tile_state<MODE>(su[so + c * ndp], MODE == kModeJvExact ? sv[so + c * ndp] : T(0));
       V f[DIM][R];
       V lam[DIM];
       P::flux_all_speed(u, f, lam, k);
@@ -132,8 +149,8 @@ __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant_
     __syncthreads();
     // ---- 2. volume term
     for (int t = tid; t < nel * nd; t += nth) {
-      int el = t / nd, node = t - el * nd;
-      int idx[3] = {node % n, (node / n) % n, node / (n * n)};
+      const int el = t / nd, node = t - el * nd;
+      const int idx[3] = {node % n, (node / n) % n, node / (n * n)};
       const V* sfe = sf + (size_t)el * DIM * R * ndp;
       V acc[R];
 #pragma unroll
@@ -156,94 +173,123 @@ __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant_
       for (int c = 0; c < R; ++c) sre[c * ndp + node] = acc[c];
     }
     __syncthreads();
-    // ---- 3. face corrections, one direction at a time (no two face points of a
-    //         direction touch the same node when n >= 2)
+    // ---- 3. face corrections, one direction at a time.  Items [0, nel*nf) are the
+    //         upper faces (+e_a) of the CTA's elements: a face whose neighbour is
+    //         also in this CTA is computed once and applied to both sides from
+    //         shared memory.  Items [nel*nf, 2*nel*nf) are the lower faces whose
+    //         neighbour lies outside the CTA (the others were done by the
+    //         neighbour's upper item).  Within a direction no two items touch the
+    //         same node (n >= 2).
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      for (int t = tid; t < nel * 2 * nf; t += nth) {
-        int el = t / (2 * nf);
-        int rem = t - el * 2 * nf;
-        int side = rem / nf;  // 0: lower face (normal -e_a), 1: upper face (normal +e_a)
-        int fidx = rem - side * nf;
+      const T g = k.ginv[a] * k.winv_end;
+      for (int t = tid; t < 2 * nel * nf; t += nth) {
+        const int side = t < nel * nf ? 1 : 0;  // 1: upper face (normal +e_a), 0: lower face
+        const int tt = side ? t : t - nel * nf;
+        const int el = tt / nf;
+        const int fidx = tt - el * nf;
         // own node: insert i_a into the face index
-        int lo = fidx % strides[a];
-        int hi = fidx / strides[a];
-        int ia_own = side ? n - 1 : 0;
-        int own = lo + ia_own * strides[a] + hi * strides[a] * n;
-        int nbr_node = lo + (n - 1 - ia_own) * strides[a] + hi * strides[a] * n;
+        const int lo = fidx % strides[a];
+        const int hi = fidx / strides[a];
+        const int ia_own = side ? n - 1 : 0;
+        const int own = lo + ia_own * strides[a] + hi * strides[a] * n;
+        const int nbr_node = lo + (n - 1 - ia_own) * strides[a] + hi * strides[a] * n;
         // neighbour element (periodic)
-        long long e = e0 + el;
-        long long ex = e % k.K[0];
-        long long ey = (e / k.K[0]) % k.K[1];
-        long long ez = e / ((long long)k.K[0] * k.K[1]);
-        long long ec[3] = {ex, ey, ez};
+        const long long e = e0 + el;
+        long long ec[3] = {e % k.K[0], (e / k.K[0]) % k.K[1], e / ((long long)k.K[0] * k.K[1])};
         ec[a] += side ? 1 : -1;
         if (ec[a] < 0) ec[a] += k.K[a];
         if (ec[a] >= k.K[a]) ec[a] -= k.K[a];
-        long long en = (ec[2] * k.K[1] + ec[1]) * k.K[0] + ec[0];
-        size_t gofs = ((size_t)en * s + m) * nd * R + (size_t)nbr_node * R;
-        size_t so = ((size_t)(el * s + m) * R) * ndp + own;
-        V um[R], up[R], fp[R], fm[R];
+        const long long en = (ec[2] * k.K[1] + ec[1]) * k.K[0] + ec[0];
+        const long long eln = en - e0;
+        const bool internal = eln >= 0 && eln < nel;
+        if (!side && internal) continue;  // computed by the neighbour's upper item
+        const size_t so = ((size_t)el * R) * ndp + own;
         const V* sfe = sf + (size_t)el * DIM * R * ndp;
+        V um[R], up[R], fm[R], fp[R];
 #pragma unroll
         for (int c = 0; c < R; ++c) {
           fm[c] = sfe[(a * R + c) * ndp + own];
-          const bool hasv = MODE != kModeResidual;
-          um[c] = eval_state<MODE>(su[so + c * ndp], hasv ? sv[so + c * ndp] : T(0), k.eps);
-          up[c] = eval_state<MODE>(k.U[gofs + c], hasv ? k.vscale * k.v[gofs + c] : T(0), k.eps);
+          um[c] = tile_state<MODE>(su[so + c * ndp], MODE == kModeJvExact ? sv[so + c * ndp] : T(0));
         }
         const V lm = sl[((size_t)el * DIM + a) * ndp + own];
-        const V lp = P::flux_speed(up, a, fp, k);
-        V* sre = sr + (size_t)el * R * ndp;
-        const T g = k.ginv[a] * k.winv_end;
-        if (side) {  // uL = u-, uR = u+ ; F -= g (H - f(u-))
-          V lam = dmax(lm, lp);
+        V lp;
+        if (internal) {
+          const size_t son = ((size_t)eln * R) * ndp + nbr_node;
+          const V* sfn = sf + (size_t)eln * DIM * R * ndp;
 #pragma unroll
           for (int c = 0; c < R; ++c) {
-            V H = T(0.5) * (fm[c] + fp[c]) - T(0.5) * (lam * (up[c] - um[c]));
-            sre[c * ndp + own] = sre[c * ndp + own] - g * (H - fm[c]);
+            fp[c] = sfn[(a * R + c) * ndp + nbr_node];
+            up[c] = tile_state<MODE>(su[son + c * ndp], MODE == kModeJvExact ? sv[son + c * ndp] : T(0));
           }
-        } else {     // uL = u+, uR = u- ; F += g (H - f(u-))
-          V lam = dmax(lp, lm);
+          lp = sl[((size_t)eln * DIM + a) * ndp + nbr_node];
+        } else {
+          const size_t gofs = ((size_t)en * s + m) * tnode + (size_t)nbr_node * R;
+#pragma unroll
+          for (int c = 0; c < R; ++c)
+            up[c] = eval_state<MODE>(k.U[gofs + c], MODE == kModeResidual ? T(0) : k.vscale * k.v[gofs + c],
+                                     k.eps);
+          lp = P::flux_speed(up, a, fp, k);
+        }
+        V* sre = sr + (size_t)el * R * ndp;
+        if (side) {  // own element below the face: uL = u-, uR = u+
+          const V lam = dmax(lm, lp);
+          V* srn = sr + (size_t)(internal ? eln : el) * R * ndp;
 #pragma unroll
           for (int c = 0; c < R; ++c) {
-            V H = T(0.5) * (fp[c] + fm[c]) - T(0.5) * (lam * (um[c] - up[c]));
+            const V H = T(0.5) * (fm[c] + fp[c]) - T(0.5) * (lam * (up[c] - um[c]));
+            sre[c * ndp + own] = sre[c * ndp + own] - g * (H - fm[c]);  // n = +e_a
+            if (internal) srn[c * ndp + nbr_node] = srn[c * ndp + nbr_node] + g * (H - fp[c]);  // n = -e_a
+          }
+        } else {     // own element above the face: uL = u+, uR = u-
+          const V lam = dmax(lp, lm);
+#pragma unroll
+          for (int c = 0; c < R; ++c) {
+            const V H = T(0.5) * (fp[c] + fm[c]) - T(0.5) * (lam * (um[c] - up[c]));
             sre[c * ndp + own] = sre[c * ndp + own] + g * (H - fm[c]);
           }
         }
       }
       __syncthreads();
     }
-    // ---- 4. temporal coupling and output (coalesced: consecutive threads write
-    //         consecutive values of the element's [node][c] block)
+    // ---- 4. temporal coupling and output (coalesced: consecutive threads read and
+    //         write consecutive values of the element's [node][c] block)
+    //         out = sum_j cm_j x_j - [m = s-1] ce x_m + cfac * (spatial term), with the
+    //         direction scale, the GMRES left scaling 1/omega_m and 1/eps folded in.
     {
-      const T hw = k.half_dt * k.omega[m];
-      for (int t = tid; t < nel * nd * R; t += nth) {
-        int c = t % R;
-        int r2 = t / R;
-        int node = r2 % nd;
-        int el = r2 / nd;
-        size_t g = ((size_t)(e0 + el) * s + m) * nd * R + (size_t)node * R + c;
-        V Fv = sr[((size_t)el * R + c) * ndp + node];
-        const T* tile = (MODE == kModeResidual) ? su : sv;
+      const bool ls = MODE != kModeResidual && k.lscale;
+      const T sm = ls ? k.inv_omega[m] : T(1);
+      const T vs = MODE == kModeResidual ? T(1) : k.vscale;
+      const T hw = ls ? k.half_dt : k.half_dt * k.omega[m];
+      const T cfac = MODE == kModeJvFD ? hw * k.inv_eps : hw;
+      T cm[NTX];
+#pragma unroll
+      for (int j = 0; j < NTX; ++j) cm[j] = (FIXED || j < s) ? (sm * vs) * sC[j * kMaxS + m] : T(0);
+      const T ce = sm * vs;
+      for (int t = tid; t < nel * (int)tnode; t += nth) {
+        const int c = t % R;
+        const int r2 = t / R;
+        const int node = r2 % nd;
+        const int el = r2 / nd;
+        const size_t gb = (size_t)(e0 + el) * s * tnode + (size_t)node * R + c;  // (e, j = 0, node, c)
+        const size_t g = gb + (size_t)m * tnode;
+        const V Fv = sr[((size_t)el * R + c) * ndp + node];
         T lin = T(0);
 #pragma unroll
         for (int j = 0; j < NTX; ++j)
-          if (FIXED || j < s) lin += sC[j * kMaxS + m] * tile[((size_t)(el * s + j) * R + c) * ndp + node];
-        if (m == s - 1) lin -= tile[((size_t)(el * s + m) * R + c) * ndp + node];
+          if (FIXED || j < s) lin += cm[j] * gtile[gb + (size_t)j * tnode];
+        if (m == s - 1) lin -= ce * gtile[g];
         if (MODE == kModeResidual) {
           // u_prev is only read when R is written (F-only launches pass no u_prev)
           if (k.out) {
-            if (m == 0) lin += k.uprev[(size_t)(e0 + el) * nd * R + (size_t)node * R + c];
-            k.out[g] = lin + hw * val(Fv);
+            if (m == 0) lin += k.uprev[(size_t)(e0 + el) * tnode + (size_t)node * R + c];
+            k.out[g] = lin + cfac * val(Fv);
           }
           if (k.fout) k.fout[g] = val(Fv);
         } else if (MODE == kModeJvFD) {
-          const T dF = (val(Fv) - k.F0[g]) * k.inv_eps;
-          k.out[g] = k.lscale ? fma(k.inv_omega[m], lin, k.half_dt * dF) : fma(hw, dF, lin);
+          k.out[g] = fma(cfac, val(Fv) - k.F0[g], lin);
         } else {
-          const T dF = tangent(Fv);
-          k.out[g] = k.lscale ? fma(k.inv_omega[m], lin, k.half_dt * dF) : fma(hw, dF, lin);
+          k.out[g] = fma(cfac, tangent(Fv), lin);
         }
       }
     }

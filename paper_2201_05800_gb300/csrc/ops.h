@@ -21,9 +21,10 @@ inline size_t operator_smem_bytes(int dim, int r, size_t tsize, int mode, int n,
   int nd = 1;
   for (int a = 0; a < dim; ++a) nd *= n;
   size_t ndp = (size_t)(nd | 1);
+  (void)s;
   size_t vbytes = mode == kModeJvExact ? 2 * tsize : tsize;
-  size_t b = (size_t)epb * s * r * ndp * tsize;
-  if (mode != kModeResidual) b += (size_t)epb * s * r * ndp * tsize;
+  size_t b = (size_t)epb * r * ndp * tsize;
+  if (mode == kModeJvExact) b += (size_t)epb * r * ndp * tsize;
   b += (size_t)epb * dim * r * ndp * vbytes;
   b += (size_t)epb * r * ndp * vbytes;
   b += (size_t)epb * dim * ndp * vbytes;
