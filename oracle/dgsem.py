@@ -121,7 +121,66 @@ def spatial_operator(grid, u):
         sl_lo = [slice(None)] * u.ndim
         sl_lo[ax_n] = 0
         L[tuple(sl_lo)] += np.roll(HS, 1, axis=ax_e)  # n = -e_a on the neighbour's lower face
+    nu = grid.params.get("viscosity", 0.0)
+    if nu:
+        L -= sipg_form(grid, u, nu)
     return L / (J * W)
+
+
+def penalty(grid):
+    """Interior-penalty parameter eta = 10 p^2 of the paper's UFL code (Sec. 4), p = N."""
+    return grid.params.get("penalty", 10.0 * grid.N ** 2)
+
+
+def sipg_form(grid, u, nu):
+    """B(u, psi_I) for every test function psi_I: the symmetric interior penalty form of
+    -nu Laplace(u) (F_v = nu grad u, Eq. general; H_v^IP of Sec. 3.1 with eta = 10 p^2 and
+    h_e = |E| / |e| = h_a on a face normal to e_a), LGL quadrature on volume and faces:
+
+      B(u, psi) = sum_E int_E nu grad u . grad psi
+                - sum_F int_F ( {nu grad u} . [[psi]] + {nu grad psi} . [[u]] )
+                + sum_F int_F sigma [[u]] . [[psi]],       sigma = nu eta / h_e,
+
+    with [[v]] = v_L - v_R and {v} = (v_L + v_R)/2 on the face between the element
+    below (L) and above (R) it in direction a.  Reading: the paper's printed surface
+    terms disagree in sign between Eq. surfaceint and the UFL listing; this is the
+    standard symmetric form, consistent with d_t u = nu Laplace(u)."""
+    d, n = grid.dim, grid.n
+    J = grid.jacobian()
+    W = grid.node_weights()[..., None]
+    eta = penalty(grid)
+    B = np.zeros_like(u)
+    for a in range(d):
+        ax_e, ax_n = grid.elem_axis(a), grid.node_axis(a)
+        ga = 2.0 / grid.h[a]
+        # gradient component a at every node: (2/h_a) sum_j D[k, j] u_j along the line
+        g = ga * np.moveaxis(np.tensordot(u, grid.D, axes=([ax_n], [1])), -1, ax_n)
+        # volume: sum_K J w_K nu g_K (2/h_a) D[k_a, i_a]
+        B += ga * np.moveaxis(np.tensordot(J * W * nu * g, grid.D, axes=([ax_n], [0])), -1, ax_n)
+        # faces normal to e_a
+        uL = _take(u, ax_n, n - 1)
+        uR = np.roll(_take(u, ax_n, 0), -1, axis=ax_e)
+        gL = _take(g, ax_n, n - 1)
+        gR = np.roll(_take(g, ax_n, 0), -1, axis=ax_e)
+        jump = uL - uR
+        avg = 0.5 * (gL + gR)
+        sigma = nu * eta / grid.h[a]
+        JWf = (J / (grid.h[a] / 2.0)) * _face_weights(grid, a)
+        sl_hi = [slice(None)] * u.ndim
+        sl_hi[ax_n] = n - 1
+        sl_lo = [slice(None)] * u.ndim
+        sl_lo[ax_n] = 0
+        # psi of the element below the face: [[psi]] = psi at its node n-1,
+        # {grad_a psi} = (1/2)(2/h_a) D[n-1, i_a]
+        B[tuple(sl_hi)] += JWf * (-nu * avg + sigma * jump)
+        line = [1] * u.ndim
+        line[ax_n] = n
+        B -= np.expand_dims(JWf * nu * 0.5 * ga * jump, ax_n) * grid.D[n - 1].reshape(line)
+        # psi of the element above the face: [[psi]] = -psi at its node 0,
+        # {grad_a psi} = (1/2)(2/h_a) D[0, i_a]
+        B[tuple(sl_lo)] += np.roll(JWf * (nu * avg - sigma * jump), 1, axis=ax_e)
+        B -= np.roll(np.expand_dims(JWf * nu * 0.5 * ga * jump, ax_n), 1, axis=ax_e) * grid.D[0].reshape(line)
+    return B
 
 
 def _face_weights(grid, a):
