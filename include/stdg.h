@@ -76,9 +76,20 @@ enum { STDG_HOST = 0, STDG_DEVICE = 1 };
 /* GMRES preconditioning of J dU = -R.  STDG_PRECOND_TEMPORAL_MASS solves the
  * left-scaled system (M_tau^-1 (x) I) J dU = -(M_tau^-1 (x) I) R: the rows of
  * temporal node m are divided by the LGL weight omega_m (a diagonal scaling;
- * the inner tolerance gmres_rtol then refers to the scaled residual).  The
- * Newton test always uses the unscaled ||R||_2. */
-enum { STDG_PRECOND_NONE = 0, STDG_PRECOND_TEMPORAL_MASS = 1 };
+ * the inner tolerance gmres_rtol then refers to the scaled residual).
+ * STDG_PRECOND_POINT_BLOCK solves J P^-1 y = -R, dU = P^-1 y (right
+ * preconditioning, so gmres_rtol refers to the true linear residual) with the
+ * block of J that couples the s temporal nodes of one spatial node I: the
+ * temporal part (D_tau^T M_tau - e_s e_s^T) of Eq. Jacobian_ST plus
+ * dt/2 M_tau times the diagonal of the spatial Jacobian at I, which for the
+ * Rusanov flux (Eq. flux:llf) is -sum over the faces through I of
+ * lambda / (h_a w_end) (wave speed derivative dropped); one s x s matrix per
+ * spatial node, rebuilt at every Newton step.  It pays on small grids (2D
+ * vortex, 8 x 8 quads, N = 4, s = 4: 141 -> 90 GMRES iterations per slab) but
+ * hardly on the 64 x 64 grid (108 -> 103), where the default
+ * STDG_PRECOND_TEMPORAL_MASS is cheaper.  The Newton test always uses the
+ * unscaled ||R||_2. */
+enum { STDG_PRECOND_NONE = 0, STDG_PRECOND_TEMPORAL_MASS = 1, STDG_PRECOND_POINT_BLOCK = 2 };
 
 typedef struct {
   int dim;                  /* spatial dimension d, 1..3                                 */
@@ -100,7 +111,7 @@ typedef struct {
   double gmres_rtol;        /* inner tolerance eta (relative to ||R||)                   */
   int gmres_maxit;          /* total inner iterations per Newton step, >= 1              */
   size_t hbm_budget_bytes;  /* 0 = unlimited; else create fails with STDG_ERR_OOM above  */
-  int precond;              /* STDG_PRECOND_NONE | STDG_PRECOND_TEMPORAL_MASS (default)  */
+  int precond;              /* STDG_PRECOND_NONE | _TEMPORAL_MASS (default) | _POINT_BLOCK */
 } stdg_config_desc;
 
 typedef struct {
@@ -165,13 +176,21 @@ stdg_status stdg_spatial_operator(stdg_ctx* ctx, const double* U, double* F, int
 stdg_status stdg_jv_fd_apply(stdg_ctx* ctx, const double* U, const double* F0, const double* v, double eps,
                              double* Jv);
 
+/* z = (P(U)^-1 (x) I_r) v with the point-block matrices P_I of
+ * STDG_PRECOND_POINT_BLOCK built from the slab U (U, v, z: slab_len values).
+ * For linear advection P_I (x) I_r is exactly the block of Eq. Jacobian_ST
+ * that couples the temporal nodes and components of spatial node I.  FP64;
+ * the library allocates the P^-1 storage of the context on the first call. */
+stdg_status stdg_precond_apply(stdg_ctx* ctx, const double* U, const double* v, double* z, int ptr_kind);
+
 /* Kernel timing inside the library: when enabled, every kernel launch is
  * bracketed by CUDA events on the context stream and its device time is
  * summed per class: 0 space-time residual / F(U), 1 Jacobian-vector product,
- * 2 Gram-Schmidt and other vector kernels of GMRES, 3 other (slab copies). */
+ * 2 Gram-Schmidt and other vector kernels of GMRES, 3 other (slab copies),
+ * 4 point-block preconditioner (build and apply). */
 typedef struct {
-  int launches[4];
-  double ms[4];
+  int launches[5];
+  double ms[5];
 } stdg_profile;
 stdg_status stdg_profile_enable(stdg_ctx* ctx, int on);
 /* Synchronises the context stream, returns the sums since the last reset. */

@@ -5,8 +5,9 @@
 // solver, as in the paper's 3D runs): U0 = 1 (x) u^n; while ||R(U)|| is above
 // max(rtol ||R(U0)||, atol): solve J(U) dU = -R(U) by restarted GMRES(m) with
 // classical Gram-Schmidt and selective re-orthogonalisation, Givens rotations
-// on the host, matrix-free J v by the space-time operator kernel, optional left
-// scaling by M_tau^-1; U += dU.  Then u^{n+1} = U^s (Eq. un).
+// on the host, matrix-free J v by the space-time operator kernel, right
+// preconditioning by the point-block inverse P^-1 (precond.cuh) or left scaling
+// by M_tau^-1; U += dU.  Then u^{n+1} = U^s (Eq. un).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -19,6 +20,7 @@
 #include "common.cuh"
 #include "lgl_host.h"
 #include "ops.h"
+#include "precond.cuh"
 #include "stdg.h"
 
 using namespace stdg;
@@ -28,6 +30,7 @@ namespace {
 constexpr int kMaxGmresM = kMaxDots - 1;  // basis of m+1 vectors must fit one dot pass
 constexpr size_t kSmemLimit = 227 * 1024;
 constexpr int kSmall = 256;               // doubles of device / pinned scratch
+constexpr int kProfClasses = 5;           // residual, Jv, Gram-Schmidt/vector, other, preconditioner
 
 }  // namespace
 
@@ -46,6 +49,10 @@ struct stdg_ctx {
   int nblk = 1;
   // FP32 buffers of the mixed-precision Krylov solve (STDG_MIXED_FP32 only)
   float *U32 = nullptr, *F032 = nullptr, *R32 = nullptr, *X32 = nullptr, *V32 = nullptr;
+  // point-block preconditioner (STDG_PRECOND_POINT_BLOCK): P_I^-1 per spatial node, in the
+  // working precision of the Krylov solve, and the preconditioned direction z = P^-1 v
+  double* Pinv64 = nullptr;
+  float *Pinv32 = nullptr, *Z32 = nullptr;
   std::vector<void*> allocs;
   size_t bytes = 0;
   double *U = nullptr, *R = nullptr, *F0 = nullptr, *delta = nullptr, *uprev = nullptr;
@@ -58,8 +65,8 @@ struct stdg_ctx {
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_live;
-  int prof_launches[4] = {0, 0, 0, 0};
-  double prof_ms[4] = {0, 0, 0, 0};
+  int prof_launches[kProfClasses] = {};
+  double prof_ms[kProfClasses] = {};
 };
 
 namespace {
@@ -203,7 +210,9 @@ stdg_status validate(const stdg_config_desc* d, std::string* why) {
   if (d->newton_maxit < 1 || d->gmres_maxit < 1) return bad("maxit must be >= 1");
   if (d->gmres_m < 1 || d->gmres_m > kMaxGmresM) return bad("gmres_m must be 1..31");
   if (!(d->newton_rtol >= 0) || !(d->newton_atol >= 0) || !(d->gmres_rtol > 0)) return bad("bad tolerance");
-  if (d->precond != STDG_PRECOND_NONE && d->precond != STDG_PRECOND_TEMPORAL_MASS) return bad("unknown precond");
+  if (d->precond != STDG_PRECOND_NONE && d->precond != STDG_PRECOND_TEMPORAL_MASS &&
+      d->precond != STDG_PRECOND_POINT_BLOCK)
+    return bad("unknown precond");
   return STDG_OK;
 }
 
@@ -277,10 +286,16 @@ struct KView {
   T* R;   // Newton residual in T
   T* X;   // slab scratch in T
   T* V;   // Krylov basis, gmres_m + 1 rows
+  T* Z;   // preconditioned direction P^-1 v (point-block preconditioner)
+  T* Pinv;  // P_I^-1 per spatial node (point-block preconditioner)
 };
 
-KView<double> view(stdg_ctx* c, double*) { return {&c->a64, c->epb64, c->U, c->F0, c->R, c->X1, c->V}; }
-KView<float> view(stdg_ctx* c, float*) { return {&c->a32, c->epb32, c->U32, c->F032, c->R32, c->X32, c->V32}; }
+KView<double> view(stdg_ctx* c, double*) {
+  return {&c->a64, c->epb64, c->U, c->F0, c->R, c->X1, c->V, c->X2, c->Pinv64};
+}
+KView<float> view(stdg_ctx* c, float*) {
+  return {&c->a32, c->epb32, c->U32, c->F032, c->R32, c->X32, c->V32, c->Z32, c->Pinv32};
+}
 
 // F(U) only, in precision T (FD Jv base point of the mixed path)
 template <class T>
@@ -373,6 +388,7 @@ stdg_status gmres(stdg_ctx* c, double eps_u, int* its_out, int* jv_out) {
   const int m = c->d.gmres_m;
   const size_t L = c->slab_len;
   const bool ls = c->d.precond == STDG_PRECOND_TEMPORAL_MASS;
+  const bool pb = c->d.precond == STDG_PRECOND_POINT_BLOCK;
   const int blk = c->nd * c->r;
   TimeWeights winv;  // left scaling of the rows of temporal node m (1 without preconditioning)
   for (int q = 0; q < 8; ++q) winv.w[q] = (ls && q < c->s) ? 1.0 / (double)c->a64.omega[q] : 1.0;
@@ -415,7 +431,14 @@ stdg_status gmres(stdg_ctx* c, double eps_u, int* its_out, int* jv_out) {
     bool done = false;
     for (int j = 0; j < m && its < c->d.gmres_maxit; ++j) {
       T* w = Vrow(j + 1);
-      CKS(op_jv_t<T>(c, kv, kv.U, kv.F0, Vrow(j), sig[j], eps_u, w, ls));
+      if (pb) {
+        // right preconditioning: w = J z with z = P^-1 v_j (|v_j| = 1, so the FD step
+        // eps_u / |v_j| is kept; |z| is within the norm bounds of P^-1)
+        PK(c, 4, (pb_apply<T, T, T>(kv.Z, Vrow(j), sig[j], kv.Pinv, 0, c->nelem, c->s, c->nd, c->r, c->st)));
+        CKS(op_jv_t<T>(c, kv, kv.U, kv.F0, kv.Z, 1.0, eps_u, w, false));
+      } else {
+        CKS(op_jv_t<T>(c, kv, kv.U, kv.F0, Vrow(j), sig[j], eps_u, w, ls));
+      }
       ++jvs;
       // p_i = V_i . w (i <= j) and |w|^2 in one pass over rows 0..j+1
       CKS(dots_to_small<T>(c, kv.V, j + 2, w, 0));
@@ -475,7 +498,14 @@ stdg_status gmres(stdg_ctx* c, double eps_u, int* its_out, int* jv_out) {
     if (kdim > 0) {
       Coefs cf;
       for (int i = 0; i < kdim; ++i) cf.c[i] = -y[i] * sig[i];
-      PK(c, 2, (update<T, double>(c->delta, kv.V, L, kdim, cf, L, c->st)));
+      if (pb) {
+        // delta += P^-1 (sum_i y_i v_i), the sum formed in the scratch row X
+        CK(c, cudaMemsetAsync(kv.X, 0, L * sizeof(T), c->st));
+        PK(c, 2, (update<T, T>(kv.X, kv.V, L, kdim, cf, L, c->st)));
+        PK(c, 4, (pb_apply<T, T, double>(c->delta, kv.X, 1.0, kv.Pinv, 1, c->nelem, c->s, c->nd, c->r, c->st)));
+      } else {
+        PK(c, 2, (update<T, double>(c->delta, kv.V, L, kdim, cf, L, c->st)));
+      }
     }
     if (done) break;
   }
@@ -560,6 +590,8 @@ stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ct
   c->nblk = 4 * c->sms;
   const size_t L = c->slab_len, S = c->state_len;
   const size_t nbasis = L * (size_t)(desc->gmres_m + 1);
+  const bool pbp = desc->precond == STDG_PRECOND_POINT_BLOCK;
+  const size_t npinv = (size_t)c->nelem * c->nd * c->s * c->s;
   stdg_status st = STDG_OK;
   if ((st = alloc(c, &c->U, L)) || (st = alloc(c, &c->R, L)) || (st = alloc(c, &c->F0, L)) ||
       (st = alloc(c, &c->delta, L)) || (st = alloc(c, &c->X1, L)) || (st = alloc(c, &c->X2, L)) ||
@@ -567,6 +599,8 @@ stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ct
       (!mixed && (st = alloc(c, &c->V, nbasis))) ||
       (mixed && ((st = alloc(c, &c->U32, L)) || (st = alloc(c, &c->F032, L)) || (st = alloc(c, &c->R32, L)) ||
                  (st = alloc(c, &c->X32, L)) || (st = alloc(c, &c->V32, nbasis)))) ||
+      (pbp && !mixed && (st = alloc(c, &c->Pinv64, npinv))) ||
+      (pbp && mixed && ((st = alloc(c, &c->Pinv32, npinv)) || (st = alloc(c, &c->Z32, L)))) ||
       (st = alloc(c, &c->partials, (size_t)c->nblk * kPartialStride)) || (st = alloc(c, &c->small, kSmall))) {
     stdg_destroy(c);
     return st;
@@ -745,6 +779,10 @@ stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
     double nu;
     CKS(norm2<double>(c, c->U, L, &nu));
     int its = 0, jvs = 0;
+    if (c->d.precond == STDG_PRECOND_POINT_BLOCK) {
+      if (mixed) PK(c, 4, (pb_build<float>(c->dim, c->d.equation, c->a64, c->U, c->Pinv32, c->st)));
+      else PK(c, 4, (pb_build<double>(c->dim, c->d.equation, c->a64, c->U, c->Pinv64, c->st)));
+    }
     if (mixed) {
       // inner solve in FP32 around the FP32 copy of the Newton iterate; the
       // FP64 residual below refines (iterative refinement)
@@ -803,6 +841,29 @@ stdg_status stdg_jv_fd_apply(stdg_ctx* c, const double* U, const double* F0, con
   return STDG_OK;
 }
 
+stdg_status stdg_precond_apply(stdg_ctx* c, const double* U, const double* v, double* z, int kind) {
+  if (!c || !U || !v || !z || (kind != STDG_HOST && kind != STDG_DEVICE)) return STDG_ERR_INVALID_ARG;
+  DevGuard g(c->device);
+  if (!c->Pinv64) CKS(alloc(c, &c->Pinv64, (size_t)c->nelem * c->nd * c->s * c->s));
+  const double* dU = U;
+  const double* dv = v;
+  double* dz = z;
+  if (kind == STDG_HOST) {
+    CK(c, cudaMemcpyAsync(c->X1, U, c->slab_len * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(c, cudaMemcpyAsync(c->X2, v, c->slab_len * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    dU = c->X1;
+    dv = c->X2;
+    dz = c->R;
+  }
+  PK(c, 4, (pb_build<double>(c->dim, c->d.equation, c->a64, dU, c->Pinv64, c->st)));
+  PK(c, 4, (pb_apply<double, double, double>(dz, dv, 1.0, c->Pinv64, 0, c->nelem, c->s, c->nd, c->r, c->st)));
+  if (kind == STDG_HOST) {
+    CK(c, cudaMemcpyAsync(z, dz, c->slab_len * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+  }
+  return STDG_OK;
+}
+
 stdg_status stdg_profile_enable(stdg_ctx* c, int on) {
   if (!c) return STDG_ERR_INVALID_ARG;
   c->prof = on != 0;
@@ -814,7 +875,7 @@ stdg_status stdg_profile_read(stdg_ctx* c, stdg_profile* out, int reset) {
   DevGuard g(c->device);
   CK(c, cudaStreamSynchronize(c->st));
   prof_collect(c);
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < kProfClasses; ++i) {
     out->launches[i] = c->prof_launches[i];
     out->ms[i] = c->prof_ms[i];
     if (reset) {

@@ -18,7 +18,7 @@ FLUX_RUSANOV = 0
 FP64, MIXED_FP32 = 0, 1
 JV_FD, JV_EXACT = 0, 1
 HOST, DEVICE = 0, 1
-PRECOND_NONE, PRECOND_TEMPORAL_MASS = 0, 1
+PRECOND_NONE, PRECOND_TEMPORAL_MASS, PRECOND_POINT_BLOCK = 0, 1, 2
 
 STATUS = {0: "STDG_OK", 1: "STDG_ERR_INVALID_ARG", 2: "STDG_ERR_OOM", 3: "STDG_ERR_CUDA",
           4: "STDG_ERR_NOT_CONVERGED", 5: "STDG_ERR_GMRES_BREAKDOWN", 6: "STDG_ERR_NAN",
@@ -47,10 +47,10 @@ class stdg_slab_stats(ctypes.Structure):
 
 
 class stdg_profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int * 4), ("ms", ctypes.c_double * 4)]
+    _fields_ = [("launches", ctypes.c_int * 5), ("ms", ctypes.c_double * 5)]
 
 
-PROFILE_CLASSES = ("residual", "jv", "gram_schmidt", "other")
+PROFILE_CLASSES = ("residual", "jv", "gram_schmidt", "other", "precond")
 
 
 class StdgError(RuntimeError):
@@ -80,6 +80,7 @@ _SIGS = {
     "stdg_slab_norm": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "stdg_spatial_operator": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "stdg_jv_fd_apply": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, _P]),
+    "stdg_precond_apply": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
     "stdg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "stdg_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(stdg_profile), ctypes.c_int]),
     "stdg_last_error": (ctypes.c_char_p, [_P]),
@@ -246,6 +247,16 @@ class Context:
         if any(k != DEVICE for _, k in ptrs):
             raise TypeError("jv_fd_apply takes device tensors")
         self._check(self._lib.stdg_jv_fd_apply(self._h, ptrs[0][0], ptrs[1][0], ptrs[2][0], float(eps), ptrs[3][0]))
+        return out
+
+    def precond_apply(self, U, v, out=None):
+        """z = P(U)^-1 v with the point-block preconditioner built from the slab U."""
+        out = (np.empty(self.slab_len) if isinstance(U, np.ndarray) else U.new_empty(self.slab_len)) \
+            if out is None else out
+        ptrs = [_ptr(x, None) for x in (U, v, out)]
+        if len({k for _, k in ptrs}) != 1:
+            raise TypeError("all buffers must be on the same side (host or device)")
+        self._check(self._lib.stdg_precond_apply(self._h, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[0][1]))
         return out
 
     def profile_enable(self, on=True):

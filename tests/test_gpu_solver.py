@@ -48,10 +48,10 @@ def test_config1_advection_100_slabs(S):
     assert st["newton_its"] >= 1 and st["gmres_its"] >= 1
 
 
-@pytest.mark.parametrize("jv,precond", [("fd", 1), ("exact", 1), ("fd", 0)])
+@pytest.mark.parametrize("jv,precond", [("fd", 2), ("exact", 2), ("fd", 1), ("exact", 1), ("fd", 0)])
 def test_vortex_slab_matches_oracle(S, jv, precond):
-    """2D Euler vortex on [0,10]^2, 8x8 quads, N = 4, s = 4, CFL 0.5: one slab (with and
-    without the left temporal-mass scaling of GMRES)."""
+    """2D Euler vortex on [0,10]^2, 8x8 quads, N = 4, s = 4, CFL 0.5: one slab with the
+    point-block preconditioner (2), the left temporal-mass scaling (1) and none (0)."""
     prob = Problem(dim=2, cells=(8, 8), N=4, s=4, eq="euler", dt=1.0, lo=(0.0, 0.0), hi=(10.0, 10.0))
     X = prob.grid.coordinates()
     u0 = inputs.isentropic_vortex(X[0], X[1], center=(5.0, 5.0))
