@@ -222,6 +222,64 @@ stdg_status stdg_profile_read(stdg_ctx* ctx, stdg_profile* out, int reset);
 #define STDG_NORM_NOALLOC_MAX_LEN ((size_t)67108864) /* 4096 blocks x 16384 values */
 stdg_status stdg_slab_norm_noalloc(const double* x, size_t len, double* out, void* cuda_stream);
 
+/* ===================================================================== batch
+ * Batched slab solves (no counterpart in the paper's software, which solves
+ * one slab system at a time; Sec. 6.3 for the Newton-Krylov method itself).
+ * A batch holds many independent slab problems ("slots") of one spatial
+ * dimension and equation that may differ in grid, N, s, dt and tolerances.
+ * All slots advance together: every tick is one fixed sequence of kernel
+ * launches over all slots, with the whole Newton-GMRES state of every slot on
+ * the device (no host synchronisation inside a tick).  Per slot:
+ *   Newton on R(U) = 0 from U0 = 1 (x) u^n, FP64 residual and update
+ *   (stop: ||R||_2 <= max(newton_rtol ||R(U0)||_2, newton_atol)), each step
+ *   solving J dU = -R by flexible GMRES(gmres_m) (no restart; the step takes
+ *   the iterate after at most gmres_m iterations or at gmres_rtol), right-
+ *   preconditioned by the point-block P (STDG_PRECOND_POINT_BLOCK), with FP32
+ *   Krylov vectors and exact (forward-mode) FP32 Jacobian-vector products;
+ *   then u^{n+1} = U^s.
+ * A slot's result does not depend on the other slots (no reduction crosses
+ * slots, all reductions have a fixed order): bitwise the same alone or in a
+ * mix.  Slot memory comes from one device arena of hbm_budget_bytes
+ * allocated at creation; stdg_batch_add fails with STDG_ERR_OOM when the arena
+ * has no room (admission by memory).  One host thread at a time per batch. */
+typedef struct stdg_batch stdg_batch;
+typedef struct {
+  int dim;                  /* 1 or 2                                                    */
+  int equation;             /* STDG_ADVECTION (1D, 2D), STDG_BURGERS (2D), STDG_EULER (2D) */
+  int max_slots;            /* capacity of the slot table, >= 1                          */
+  size_t hbm_budget_bytes;  /* arena for slot vectors, > 0                               */
+} stdg_batch_desc;
+
+/* Create a batch on the current device; cuda_stream as in stdg_create. */
+stdg_status stdg_batch_create(const stdg_batch_desc* desc, void* cuda_stream, stdg_batch** out);
+stdg_status stdg_batch_destroy(stdg_batch* b);
+/* Admit one slab problem with initial state u0 (state layout, stdg_state_len
+ * values of the problem, host or device pointer).  inst->dim and
+ * inst->equation must match the batch; inst->gmres_m (1..31),
+ * newton_rtol/atol/maxit and gmres_rtol are used; precision, jv_mode, precond
+ * and gmres_maxit are ignored (see above).  *slot receives the slot id.
+ * STDG_ERR_OOM: the arena (or the slot table) is full; nothing changed. */
+stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* inst, const double* u0, int ptr_kind, int* slot);
+/* Run `ticks` ticks (>= 1), then report in *working how many admitted slots
+ * have not finished (may be NULL).  Finished slots keep their results until
+ * stdg_batch_remove. */
+stdg_status stdg_batch_step(stdg_batch* b, int ticks, int* working);
+/* Tick until no slot is working or max_ticks ticks ran. */
+stdg_status stdg_batch_run(stdg_batch* b, int max_ticks, int* working);
+/* *done = 1 once the slot's solve ended; *status = its stdg_status
+ * (STDG_OK, STDG_ERR_NOT_CONVERGED, STDG_ERR_NAN); stats may be NULL. */
+stdg_status stdg_batch_query(stdg_batch* b, int slot, int* done, int* status, stdg_slab_stats* stats);
+/* u^{n+1} of a finished slot (u0 before), state layout. */
+stdg_status stdg_batch_get_state(stdg_batch* b, int slot, double* u, int ptr_kind);
+/* The slot's last Newton iterate U (slab layout, slab_len values). */
+stdg_status stdg_batch_get_slab(stdg_batch* b, int slot, double* U, int ptr_kind);
+/* Release a slot (its arena memory becomes free for new admissions). */
+stdg_status stdg_batch_remove(stdg_batch* b, int slot);
+/* Device bytes a problem would take in the arena (0 if invalid). */
+size_t stdg_batch_slot_bytes(const stdg_batch* b, const stdg_config_desc* inst);
+size_t stdg_batch_free_bytes(const stdg_batch* b);
+const char* stdg_batch_last_error(const stdg_batch* b);
+
 const char* stdg_last_error(const stdg_ctx* ctx);
 const char* stdg_status_string(stdg_status st);
 /* Library version string. */

@@ -16,6 +16,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "args_host.cuh"
 #include "blas.cuh"
 #include "common.cuh"
 #include "lgl_host.h"
@@ -161,33 +162,7 @@ int num_components(int eq, int dim) { return eq == STDG_EULER ? dim + 2 : 1; }
 
 template <class T>
 void fill_args(const stdg_ctx* c, OpArgs<T>& k) {
-  std::memset(&k, 0, sizeof(k));
-  k.n = c->n;
-  k.s = c->s;
-  k.nd = c->nd;
-  k.K[0] = c->d.cells[0];
-  k.K[1] = c->dim > 1 ? c->d.cells[1] : 1;
-  k.K[2] = c->dim > 2 ? c->d.cells[2] : 1;
-  k.nelem = c->nelem;
-  double xi[16], w[16], D[256];
-  lgl_rule(c->n, xi, w);
-  diff_matrix(c->n, xi, D);
-  for (int i = 0; i < c->n; ++i)
-    for (int j = 0; j < c->n; ++j) k.D[i][j] = (T)D[i * c->n + j];
-  double tau[16], om[16], Dt[256];
-  lgl_rule(c->s, tau, om);
-  diff_matrix(c->s, tau, Dt);
-  // (D_tau^T M_tau)[m][j] = Dtau[j][m] omega_j  with Dtau[j][m] = l_m'(tau_j)
-  for (int j = 0; j < c->s; ++j)
-    for (int m = 0; m < c->s; ++m) k.C[j][m] = (T)(om[j] * Dt[j * c->s + m]);
-  for (int m = 0; m < c->s; ++m) k.omega[m] = (T)om[m];
-  for (int a = 0; a < 3; ++a) k.ginv[a] = (T)(a < c->dim ? 2.0 / c->h[a] : 0.0);
-  k.winv_end = (T)(1.0 / w[0]);
-  k.half_dt = (T)(0.5 * c->d.dt);
-  k.gamma = (T)c->d.gamma;
-  for (int a = 0; a < 3; ++a) k.adv[a] = (T)c->d.adv_vel[a];
-  k.vscale = (T)1;
-  for (int m = 0; m < c->s; ++m) k.inv_omega[m] = (T)(1.0 / om[m]);
+  fill_op_args<T>(k, c->dim, c->n, c->s, c->d.cells, c->h, c->d.dt, c->d.gamma, c->d.adv_vel);
 }
 
 stdg_status validate(const stdg_config_desc* d, std::string* why) {

@@ -1,0 +1,568 @@
+// Host side of the batched engine (engine.cuh): device arena, slot table,
+// work-item lists and the stdg_batch_* entry points of include/stdg.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "args_host.cuh"
+#include "engine.cuh"
+#include "engine_ops.cuh"
+#include "ops.h"
+#include "stdg.h"
+
+using namespace stdg;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kChunkValues = 16384;   // values per work item of the build / dot / update kernels
+constexpr size_t kOpSmemCap = 96 * 1024;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Best-fit allocator over one device region (offsets, kAlign-aligned sizes).
+struct Arena {
+  size_t size = 0;
+  std::map<size_t, size_t> free_;  // offset -> bytes
+  void init(size_t bytes) {
+    size = bytes;
+    free_.clear();
+    free_[0] = bytes;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = align_up(bytes);
+    auto best = free_.end();
+    for (auto it = free_.begin(); it != free_.end(); ++it)
+      if (it->second >= bytes && (best == free_.end() || it->second < best->second)) best = it;
+    if (best == free_.end()) return false;
+    *off = best->first;
+    const size_t rest = best->second - bytes;
+    const size_t roff = best->first + bytes;
+    free_.erase(best);
+    if (rest) free_[roff] = rest;
+    return true;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = align_up(bytes);
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t free_bytes() const {
+    size_t t = 0;
+    for (auto& f : free_) t += f.second;
+    return t;
+  }
+};
+
+struct Layout {
+  int n, s, nd, r, m, dim;
+  long long nelem;
+  size_t L, S, npinv;
+  size_t off_U, off_R, off_uprev, off_U32, off_Pinv, off_V, off_Z, bytes;
+};
+
+struct HostSlot {
+  bool used = false, active = false, done = false;
+  stdg_config_desc d;
+  Layout lay;
+  size_t off = 0;
+  int epb64 = 1, epb32 = 1;
+  SlotBuf buf;
+};
+
+}  // namespace
+
+struct stdg_batch {
+  stdg_batch_desc d;
+  cudaStream_t st = nullptr;
+  int device = 0, sms = 1;
+  char* arena_base = nullptr;
+  Arena arena;
+  std::vector<HostSlot> slots;
+  // device tables
+  SlotCtl* ctl = nullptr;
+  OpArgs<double>* a64 = nullptr;
+  OpArgs<float>* a32 = nullptr;
+  SlotBuf* buf = nullptr;
+  int* counts = nullptr;  // [0] op items, [1] chunk items
+  int* active_d = nullptr;
+  int* phase_d = nullptr;
+  EngItem* op_items = nullptr;
+  EngItem* chunk_items = nullptr;
+  double* partials = nullptr;
+  size_t cap_op = 0, cap_chunk = 0;
+  int* phase_h = nullptr;  // pinned
+  // host lists
+  std::vector<int> active;
+  int n_op = 0, n_chunk = 0;
+  bool dirty = true;
+  size_t smem64 = 0, smem32 = 0;
+  std::string err;
+};
+
+namespace {
+
+stdg_status bfail(stdg_batch* b, stdg_status st, const std::string& msg) {
+  if (b) b->err = msg;
+  return st;
+}
+
+#define BCK(b, expr)                                                                                  \
+  do {                                                                                                \
+    cudaError_t _e = (expr);                                                                          \
+    if (_e != cudaSuccess)                                                                            \
+      return bfail((b), STDG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));           \
+  } while (0)
+
+struct BDev {
+  int prev = -1, dev;
+  explicit BDev(int d) : dev(d) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~BDev() {
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+  }
+};
+
+int ncomp(int eq, int dim) { return eq == STDG_EULER ? dim + 2 : 1; }
+
+bool physics_supported(int dim, int eq) {
+  return (eq == STDG_ADVECTION && (dim == 1 || dim == 2)) || (eq == STDG_BURGERS && dim == 2) ||
+         (eq == STDG_EULER && dim == 2);
+}
+
+stdg_status check_inst(const stdg_batch* b, const stdg_config_desc* d, std::string* why) {
+  auto bad = [&](const char* m) { *why = m; return STDG_ERR_INVALID_ARG; };
+  if (d->dim != b->d.dim || d->equation != b->d.equation) return bad("dim/equation differ from the batch");
+  for (int a = 0; a < d->dim; ++a) {
+    if (d->cells[a] < 1) return bad("cells must be >= 1");
+    if (!(d->hi[a] > d->lo[a])) return bad("hi must exceed lo");
+  }
+  if (d->N < 1 || d->N > 7) return bad("N must be 1..7");
+  if (d->s < 2 || d->s > 5) return bad("s must be 2..5");
+  if (!(d->dt > 0) || !std::isfinite(d->dt)) return bad("dt must be positive");
+  if (d->equation == STDG_EULER && !(d->gamma > 1.0)) return bad("gamma must exceed 1");
+  if (d->gmres_m < 1 || d->gmres_m > kEngMaxM) return bad("gmres_m must be 1..31");
+  if (d->newton_maxit < 1) return bad("newton_maxit must be >= 1");
+  if (!(d->newton_rtol >= 0) || !(d->newton_atol >= 0) || !(d->gmres_rtol > 0)) return bad("bad tolerance");
+  return STDG_OK;
+}
+
+Layout layout_of(const stdg_config_desc* d) {
+  Layout l;
+  l.dim = d->dim;
+  l.n = d->N + 1;
+  l.s = d->s;
+  l.r = ncomp(d->equation, d->dim);
+  l.m = d->gmres_m;
+  l.nd = 1;
+  l.nelem = 1;
+  for (int a = 0; a < d->dim; ++a) {
+    l.nd *= l.n;
+    l.nelem *= d->cells[a];
+  }
+  l.S = (size_t)l.nelem * l.nd * l.r;
+  l.L = l.S * l.s;
+  l.npinv = (size_t)l.nelem * l.nd * l.s * l.s;
+  size_t o = 0;
+  l.off_U = o;
+  o += align_up(l.L * 8);
+  l.off_R = o;
+  o += align_up(l.L * 8);
+  l.off_uprev = o;
+  o += align_up(l.S * 8);
+  l.off_U32 = o;
+  o += align_up(l.L * 4);
+  l.off_Pinv = o;
+  o += align_up(l.npinv * 4);
+  l.off_V = o;
+  o += align_up(l.L * 4 * (size_t)(l.m + 1));
+  l.off_Z = o;
+  o += align_up(l.L * 4 * (size_t)l.m);
+  l.bytes = o;
+  return l;
+}
+
+// Largest elements-per-CTA (<= 256 / n^d nodes per CTA) whose tile fits the cap.
+int pick_epb(int dim, int eq, int tsize, int mode, int n, int s, long long nelem, int nd) {
+  const int r = ncomp(eq, dim);
+  int epb = std::max(1, 256 / nd);
+  if (epb > nelem) epb = (int)nelem;
+  while (epb > 1 && operator_smem_bytes(dim, r, tsize, mode, n, s, epb) > kOpSmemCap) --epb;
+  return epb;
+}
+
+template <class T>
+cudaError_t grow(T** p, size_t* cap, size_t need, cudaStream_t st) {
+  if (need <= *cap) return cudaSuccess;
+  size_t nc = std::max(need, *cap * 2 + 64);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  e = cudaMalloc(p, nc * sizeof(T));
+  if (e != cudaSuccess) return e;
+  *cap = nc;
+  return cudaSuccess;
+}
+
+// Work-item lists and slot records of the active slots.
+stdg_status rebuild(stdg_batch* b) {
+  std::vector<EngItem> op, ch;
+  b->smem64 = b->smem32 = 0;
+  for (int id : b->active) {
+    HostSlot& hs = b->slots[id];
+    const Layout& l = hs.lay;
+    const long long tiles = (l.nelem + hs.epb64 - 1) / hs.epb64;
+    const long long tiles32 = (l.nelem + hs.epb32 - 1) / hs.epb32;
+    // one item list serves both op kernels: tile indices valid for both epb values
+    for (long long t = 0; t < std::max(tiles, tiles32); ++t) op.push_back({id, (int)t});
+    hs.buf.item0 = (int)ch.size();
+    for (int c = 0; c < hs.buf.nitems; ++c) ch.push_back({id, c});
+    b->smem64 = std::max(b->smem64, operator_smem_bytes(l.dim, l.r, 8, kModeResidual, l.n, l.s, hs.epb64));
+    b->smem32 = std::max(b->smem32, operator_smem_bytes(l.dim, l.r, 4, kModeJvExact, l.n, l.s, hs.epb32));
+    BCK(b, cudaMemcpyAsync(b->buf + id, &hs.buf, sizeof(SlotBuf), cudaMemcpyHostToDevice, b->st));
+  }
+  BCK(b, grow(&b->op_items, &b->cap_op, std::max<size_t>(op.size(), 1), b->st));
+  size_t capc = b->cap_chunk;
+  BCK(b, grow(&b->chunk_items, &b->cap_chunk, std::max<size_t>(ch.size(), 1), b->st));
+  if (b->cap_chunk != capc || !b->partials) {
+    BCK(b, cudaStreamSynchronize(b->st));
+    if (b->partials) cudaFree(b->partials);
+    b->partials = nullptr;
+    BCK(b, cudaMalloc(&b->partials, b->cap_chunk * kEngRows * sizeof(double)));
+  }
+  if (!op.empty())
+    BCK(b, cudaMemcpyAsync(b->op_items, op.data(), op.size() * sizeof(EngItem), cudaMemcpyHostToDevice, b->st));
+  if (!ch.empty())
+    BCK(b, cudaMemcpyAsync(b->chunk_items, ch.data(), ch.size() * sizeof(EngItem), cudaMemcpyHostToDevice, b->st));
+  int cnt[2] = {(int)op.size(), (int)ch.size()};
+  BCK(b, cudaMemcpyAsync(b->counts, cnt, sizeof(cnt), cudaMemcpyHostToDevice, b->st));
+  if (!b->active.empty())
+    BCK(b, cudaMemcpyAsync(b->active_d, b->active.data(), b->active.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           b->st));
+  // the host vectors are pageable: make the copies complete before they go out of scope
+  BCK(b, cudaStreamSynchronize(b->st));
+  b->n_op = cnt[0];
+  b->n_chunk = cnt[1];
+  b->dirty = false;
+  return STDG_OK;
+}
+
+stdg_status tick(stdg_batch* b) {
+  if (b->dirty) {
+    stdg_status s = rebuild(b);
+    if (s != STDG_OK) return s;
+  }
+  if (b->active.empty()) return STDG_OK;
+  EngLaunch L;
+  L.op_items = b->op_items;
+  L.n_op_items = b->counts;
+  L.chunk_items = b->chunk_items;
+  L.n_chunk_items = b->counts + 1;
+  L.active = b->active_d;
+  L.n_active = (int)b->active.size();
+  const size_t smem = std::max(b->smem64, b->smem32);
+  const int per_sm = std::max(1, std::min(8, (int)(233472 / (smem + 1024))));
+  L.op_grid = std::max(1, std::min(b->n_op, b->sms * per_sm));
+  L.chunk_grid = std::max(1, std::min(b->n_chunk, b->sms * 8));
+  L.op_smem64 = b->smem64;
+  L.op_smem32 = b->smem32;
+  L.a64 = b->a64;
+  L.a32 = b->a32;
+  L.buf = b->buf;
+  L.ctl = b->ctl;
+  L.partials = b->partials;
+  cudaError_t e;
+  if (b->d.equation == STDG_EULER && b->d.dim == 2) e = eng_physics_euler2(L, b->st);
+  else if (b->d.equation == STDG_BURGERS && b->d.dim == 2) e = eng_physics_burgers2(L, b->st);
+  else e = eng_physics_advection(b->d.dim, L, b->st);
+  if (e != cudaSuccess) return bfail(b, STDG_ERR_CUDA, std::string("engine physics launch: ") + cudaGetErrorString(e));
+  e = eng_generic_launch(L, b->st);
+  if (e != cudaSuccess) return bfail(b, STDG_ERR_CUDA, std::string("engine launch: ") + cudaGetErrorString(e));
+  return STDG_OK;
+}
+
+__global__ void gather_phase_kernel(const int* active, int n, const SlotCtl* ctl, int* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = ctl[active[i]].phase;
+}
+
+// Drop finished slots from the active list; *working = slots still working.
+stdg_status refresh(stdg_batch* b, int* working) {
+  const int n = (int)b->active.size();
+  if (n > 0) {
+    gather_phase_kernel<<<(n + 255) / 256, 256, 0, b->st>>>(b->active_d, n, b->ctl, b->phase_d);
+    BCK(b, cudaGetLastError());
+    BCK(b, cudaMemcpyAsync(b->phase_h, b->phase_d, n * sizeof(int), cudaMemcpyDeviceToHost, b->st));
+    BCK(b, cudaStreamSynchronize(b->st));
+    std::vector<int> keep;
+    for (int i = 0; i < n; ++i) {
+      const int id = b->active[i];
+      if (b->phase_h[i] == kPhDone) {
+        b->slots[id].active = false;
+        b->slots[id].done = true;
+        b->dirty = true;
+      } else {
+        keep.push_back(id);
+      }
+    }
+    b->active.swap(keep);
+  }
+  if (working) *working = (int)b->active.size();
+  return STDG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+stdg_status stdg_batch_create(const stdg_batch_desc* desc, void* cuda_stream, stdg_batch** out) {
+  if (!out) return STDG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc || desc->max_slots < 1 || desc->hbm_budget_bytes == 0 || !physics_supported(desc->dim, desc->equation))
+    return STDG_ERR_INVALID_ARG;
+  stdg_batch* b = new stdg_batch();
+  b->d = *desc;
+  b->st = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&b->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return STDG_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (b->sms < 1) b->sms = 1;
+  const int ns = desc->max_slots;
+  b->slots.resize(ns);
+  bool ok = cudaMalloc(&b->arena_base, desc->hbm_budget_bytes) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->ctl, ns * sizeof(SlotCtl)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->a64, ns * sizeof(OpArgs<double>)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->a32, ns * sizeof(OpArgs<float>)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->buf, ns * sizeof(SlotBuf)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->counts, 2 * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->active_d, ns * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->phase_d, ns * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&b->phase_h, ns * sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    stdg_batch_destroy(b);
+    return STDG_ERR_OOM;
+  }
+  if (cudaMemsetAsync(b->ctl, 0, ns * sizeof(SlotCtl), b->st) != cudaSuccess ||
+      cudaMemsetAsync(b->counts, 0, 2 * sizeof(int), b->st) != cudaSuccess ||
+      cudaStreamSynchronize(b->st) != cudaSuccess) {
+    cudaGetLastError();
+    stdg_batch_destroy(b);
+    return STDG_ERR_CUDA;
+  }
+  b->arena.init(desc->hbm_budget_bytes);
+  *out = b;
+  return STDG_OK;
+}
+
+stdg_status stdg_batch_destroy(stdg_batch* b) {
+  if (!b) return STDG_ERR_INVALID_ARG;
+  BDev g(b->device);
+  cudaStreamSynchronize(b->st);
+  void* ps[] = {b->arena_base, b->ctl, b->a64, b->a32, b->buf, b->counts, b->active_d, b->phase_d,
+                b->op_items, b->chunk_items, b->partials};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  if (b->phase_h) cudaFreeHost(b->phase_h);
+  cudaGetLastError();
+  delete b;
+  return STDG_OK;
+}
+
+size_t stdg_batch_slot_bytes(const stdg_batch* b, const stdg_config_desc* inst) {
+  if (!b || !inst) return 0;
+  std::string why;
+  if (check_inst(b, inst, &why) != STDG_OK) return 0;
+  return layout_of(inst).bytes;
+}
+
+size_t stdg_batch_free_bytes(const stdg_batch* b) { return b ? b->arena.free_bytes() : 0; }
+
+stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* d, const double* u0, int kind, int* slot) {
+  if (!b || !d || !u0 || !slot || (kind != STDG_HOST && kind != STDG_DEVICE)) return STDG_ERR_INVALID_ARG;
+  *slot = -1;
+  std::string why;
+  if (check_inst(b, d, &why) != STDG_OK) return bfail(b, STDG_ERR_INVALID_ARG, why);
+  BDev g(b->device);
+  int id = -1;
+  for (int i = 0; i < (int)b->slots.size(); ++i)
+    if (!b->slots[i].used) {
+      id = i;
+      break;
+    }
+  if (id < 0) return bfail(b, STDG_ERR_OOM, "slot table full");
+  const Layout l = layout_of(d);
+  size_t off;
+  if (!b->arena.alloc(l.bytes, &off)) return bfail(b, STDG_ERR_OOM, "arena full");
+  HostSlot& hs = b->slots[id];
+  hs = HostSlot();
+  hs.used = true;
+  hs.active = true;
+  hs.d = *d;
+  hs.lay = l;
+  hs.off = off;
+  char* base = b->arena_base + off;
+  SlotBuf& sb = hs.buf;
+  sb.U = reinterpret_cast<double*>(base + l.off_U);
+  sb.R = reinterpret_cast<double*>(base + l.off_R);
+  sb.uprev = reinterpret_cast<double*>(base + l.off_uprev);
+  sb.U32 = reinterpret_cast<float*>(base + l.off_U32);
+  sb.Pinv = reinterpret_cast<float*>(base + l.off_Pinv);
+  sb.V = reinterpret_cast<float*>(base + l.off_V);
+  sb.Z = reinterpret_cast<float*>(base + l.off_Z);
+  sb.nelem = l.nelem;
+  sb.s = l.s;
+  sb.nd = l.nd;
+  sb.r = l.r;
+  sb.L = l.L;
+  sb.chunk_elems = std::max(1, (int)(kChunkValues / ((size_t)l.s * l.nd * l.r)));
+  sb.nitems = (int)((l.nelem + sb.chunk_elems - 1) / sb.chunk_elems);
+  sb.item0 = 0;
+  hs.epb64 = pick_epb(l.dim, d->equation, 8, kModeResidual, l.n, l.s, l.nelem, l.nd);
+  hs.epb32 = pick_epb(l.dim, d->equation, 4, kModeJvExact, l.n, l.s, l.nelem, l.nd);
+  // operator constants
+  double h[3] = {1, 1, 1};
+  for (int a = 0; a < l.dim; ++a) h[a] = (d->hi[a] - d->lo[a]) / d->cells[a];
+  OpArgs<double> k64;
+  OpArgs<float> k32;
+  fill_op_args<double>(k64, l.dim, l.n, l.s, d->cells, h, d->dt, d->gamma, d->adv_vel);
+  fill_op_args<float>(k32, l.dim, l.n, l.s, d->cells, h, d->dt, d->gamma, d->adv_vel);
+  k64.epb = hs.epb64;
+  k64.U = sb.U;
+  k64.uprev = sb.uprev;
+  k64.out = sb.R;
+  k64.fout = nullptr;
+  k32.epb = hs.epb32;
+  k32.U = sb.U32;
+  k32.v = sb.Z;
+  k32.out = sb.V + l.L;
+  k32.vscale = 1.0f;
+  k32.lscale = 0;
+  SlotCtl c;
+  std::memset(&c, 0, sizeof(c));
+  c.phase = kPhResid;
+  c.m = l.m;
+  c.newton_maxit = d->newton_maxit;
+  c.rtol = d->newton_rtol;
+  c.atol = d->newton_atol;
+  c.gmres_rtol = d->gmres_rtol;
+  c.status = STDG_OK;
+  BCK(b, cudaMemcpyAsync(b->a64 + id, &k64, sizeof(k64), cudaMemcpyHostToDevice, b->st));
+  BCK(b, cudaMemcpyAsync(b->a32 + id, &k32, sizeof(k32), cudaMemcpyHostToDevice, b->st));
+  BCK(b, cudaMemcpyAsync(b->ctl + id, &c, sizeof(c), cudaMemcpyHostToDevice, b->st));
+  BCK(b, cudaMemcpyAsync(sb.uprev, u0, l.S * sizeof(double),
+                         kind == STDG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, b->st));
+  BCK(b, eng_init_slot(sb, b->st));
+  // the staging structs live on this stack frame
+  BCK(b, cudaStreamSynchronize(b->st));
+  b->active.push_back(id);
+  b->dirty = true;
+  *slot = id;
+  return STDG_OK;
+}
+
+stdg_status stdg_batch_step(stdg_batch* b, int ticks, int* working) {
+  if (!b || ticks < 1) return STDG_ERR_INVALID_ARG;
+  BDev g(b->device);
+  for (int t = 0; t < ticks; ++t) {
+    stdg_status s = tick(b);
+    if (s != STDG_OK) return s;
+  }
+  return refresh(b, working);
+}
+
+stdg_status stdg_batch_run(stdg_batch* b, int max_ticks, int* working) {
+  if (!b || max_ticks < 1) return STDG_ERR_INVALID_ARG;
+  int done_ticks = 0, w = (int)b->active.size();
+  while (w > 0 && done_ticks < max_ticks) {
+    const int t = std::min(8, max_ticks - done_ticks);
+    stdg_status s = stdg_batch_step(b, t, &w);
+    if (s != STDG_OK) return s;
+    done_ticks += t;
+  }
+  if (working) *working = w;
+  return STDG_OK;
+}
+
+stdg_status stdg_batch_query(stdg_batch* b, int slot, int* done, int* status, stdg_slab_stats* stats) {
+  if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used) return STDG_ERR_INVALID_ARG;
+  BDev g(b->device);
+  SlotCtl c;
+  BCK(b, cudaMemcpyAsync(&c, b->ctl + slot, sizeof(c), cudaMemcpyDeviceToHost, b->st));
+  BCK(b, cudaStreamSynchronize(b->st));
+  if (done) *done = c.phase == kPhDone ? 1 : 0;
+  if (status) *status = c.status;
+  if (stats) {
+    stats->newton_its = c.newton_its;
+    stats->gmres_its = c.gmres_its;
+    stats->residual_evals = c.resid_evals;
+    stats->jv_evals = c.jv_evals;
+    stats->res0 = c.res0;
+    stats->res_final = c.res;
+  }
+  return STDG_OK;
+}
+
+stdg_status stdg_batch_get_state(stdg_batch* b, int slot, double* u, int kind) {
+  if (!b || !u || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used ||
+      (kind != STDG_HOST && kind != STDG_DEVICE))
+    return STDG_ERR_INVALID_ARG;
+  BDev g(b->device);
+  const HostSlot& hs = b->slots[slot];
+  BCK(b, cudaMemcpyAsync(u, hs.buf.uprev, hs.lay.S * sizeof(double),
+                         kind == STDG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, b->st));
+  BCK(b, cudaStreamSynchronize(b->st));
+  return STDG_OK;
+}
+
+stdg_status stdg_batch_get_slab(stdg_batch* b, int slot, double* U, int kind) {
+  if (!b || !U || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used ||
+      (kind != STDG_HOST && kind != STDG_DEVICE))
+    return STDG_ERR_INVALID_ARG;
+  BDev g(b->device);
+  const HostSlot& hs = b->slots[slot];
+  BCK(b, cudaMemcpyAsync(U, hs.buf.U, hs.lay.L * sizeof(double),
+                         kind == STDG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, b->st));
+  BCK(b, cudaStreamSynchronize(b->st));
+  return STDG_OK;
+}
+
+stdg_status stdg_batch_remove(stdg_batch* b, int slot) {
+  if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used) return STDG_ERR_INVALID_ARG;
+  BDev g(b->device);
+  // kernels of earlier ticks may still read the slot's memory
+  BCK(b, cudaStreamSynchronize(b->st));
+  HostSlot& hs = b->slots[slot];
+  if (hs.active) {
+    b->active.erase(std::find(b->active.begin(), b->active.end(), slot));
+    b->dirty = true;
+  }
+  b->arena.release(hs.off, hs.lay.bytes);
+  hs = HostSlot();
+  return STDG_OK;
+}
+
+const char* stdg_batch_last_error(const stdg_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+}  // extern "C"

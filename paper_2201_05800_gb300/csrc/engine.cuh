@@ -1,0 +1,98 @@
+// Batched, device-driven Newton-Krylov engine: many independent slab solves
+// (slots) advance together, one state-machine step per "tick".
+//
+// Every slot solves its own slab system R(U) = 0 (Eq. DG_vs_RK:DG) by Newton
+// (Sec. 6.3) with a right-preconditioned flexible GMRES(m) inner solve: the
+// point-block preconditioner of precond.cuh, the Krylov basis V, the
+// preconditioned directions Z = P^-1 V and the exact (forward-mode) FP32
+// Jacobian-vector products; the Newton residual, the solution update and the
+// Hessenberg/Givens arithmetic are FP64 (iterative refinement).  No restarts:
+// a Newton step takes the GMRES iterate after at most m iterations.
+//
+// The whole solver state of a slot lives on the device: its vectors in one
+// allocation of the engine's arena and its scalars (phase, Hessenberg matrix,
+// rotations, coefficients) in a SlotCtl record.  A tick is a fixed sequence of
+// launches over all slots, each kernel walking a list of work items
+// (slot, tile) and skipping the slots whose phase does not need it:
+//   1. build   P_I^-1 from U                       (slots in kPhResid)
+//   2. op      R(U) in FP64                        (kPhResid)
+//   3. op      w = J z_j in FP32                   (kPhArnoldi)
+//   4. dot     |R|^2, or V_i . w for i <= j + 1    (kPhResid, kPhArnoldi, kPhReorth)
+//   5. control one warp per slot: sums its partials in a fixed order, then
+//              Newton test / Hessenberg column / Givens rotation / triangular
+//              solve, and picks the next phase and this tick's update
+//   6. update  w -= V c, z = P^-1 (w / |w|), U += Z y, u^{n+1} = U^s
+// No host synchronisation inside a tick; slots are independent (no reduction
+// crosses slots and every reduction has a fixed order), so a slot's result
+// does not depend on which other slots share the launches.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace stdg {
+
+constexpr int kEngMaxM = 31;  // Krylov dimension: basis of m + 1 <= 32 rows
+constexpr int kEngRows = 32;
+constexpr int kEngThreads = 256;
+
+enum EngPhase { kPhIdle = 0, kPhResid = 1, kPhArnoldi = 2, kPhReorth = 3, kPhDone = 4 };
+enum EngUpd { kUpdNone = 0, kUpdInit = 1, kUpdGS = 2, kUpdGSZ = 3, kUpdSolve = 4, kUpdExtract = 5 };
+
+// Device pointers and sizes of one slot.
+struct SlotBuf {
+  double* U;      // Newton iterate, slab layout [e][m][node][c]
+  double* R;      // Newton residual
+  double* uprev;  // u^n on entry, u^{n+1} after the solve, [e][node][c]
+  float* U32;     // FP32 copy of U (base point of the Jacobian-vector products)
+  float* Pinv;    // P_I^-1 per spatial node, [e][m][j][node]
+  float* V;       // Krylov basis, m + 1 rows of L values (unnormalised, v_i = sig_i V_i)
+  float* Z;       // preconditioned directions z_i = P^-1 v_i, m rows
+  long long nelem;
+  int s, nd, r;
+  int chunk_elems;  // elements per work item of the build / dot / update kernels
+  size_t L;         // slab length nelem * s * nd * r
+  int item0, nitems;  // this slot's work items in the chunk list (control reduction)
+};
+
+// Scalar solver state of one slot (FP64).
+struct SlotCtl {
+  int phase, j, m, upd, upd_row, upd_k;
+  int newton_its, gmres_its, resid_evals, jv_evals, newton_maxit, status;
+  double rtol, atol, gmres_rtol;
+  double res0, target, res, beta, tol, zscale;
+  double coef[kEngRows];
+  double sig[kEngRows + 1];
+  double g[kEngRows + 1];
+  double cs[kEngRows], sn[kEngRows];
+  double H[kEngRows * kEngRows];  // H[i * kEngRows + j]
+};
+
+struct EngItem {
+  int slot, idx;
+};
+
+// ---- launchers (engine_kernels.cu, engine_ops_*.cu)
+struct EngLaunch {
+  const EngItem* op_items;
+  const int* n_op_items;
+  const EngItem* chunk_items;
+  const int* n_chunk_items;
+  const int* active;  // active slot ids
+  int n_active;
+  int op_grid, chunk_grid;
+  size_t op_smem64, op_smem32;
+  OpArgs<double>* a64;
+  OpArgs<float>* a32;
+  SlotBuf* buf;
+  SlotCtl* ctl;
+  double* partials;  // kEngRows per chunk item
+};
+
+// dot, control, update
+cudaError_t eng_generic_launch(const EngLaunch& L, cudaStream_t st);
+// U = 1 (x) uprev, U32 = (float) U for one slot
+cudaError_t eng_init_slot(const SlotBuf& b, cudaStream_t st);
+
+}  // namespace stdg

@@ -1,0 +1,336 @@
+// Physics-independent kernels of the batched engine (engine.cuh): the dot
+// pass, the per-slot controller and the vector update.
+#include <math.h>
+
+#include "engine.cuh"
+
+namespace stdg {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum_xor(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// element range of a chunk item
+__device__ __forceinline__ void chunk_range(const SlotBuf& b, int idx, long long* e0, long long* e1) {
+  *e0 = (long long)idx * b.chunk_elems;
+  long long hi = *e0 + b.chunk_elems;
+  *e1 = hi < b.nelem ? hi : b.nelem;
+}
+
+// partials[item][i], i < k: |R|^2 over the chunk (kPhResid) or V_i . w with
+// w = V_{j+1} (kPhArnoldi, kPhReorth; k = j + 2, per-thread sums in FP32 as in
+// the single-slab mixed path, cross-thread sums in FP64 in a fixed order).
+__global__ void __launch_bounds__(kEngThreads) eng_dot_kernel(const __grid_constant__ EngLaunch L) {
+  __shared__ double red[kEngThreads / 32][kEngRows];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int n = *L.n_chunk_items;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const EngItem item = L.chunk_items[it];
+    const int ph = L.ctl[item.slot].phase;
+    if (ph != kPhResid && ph != kPhArnoldi && ph != kPhReorth) continue;
+    const SlotBuf b = L.buf[item.slot];
+    long long e0, e1;
+    chunk_range(b, item.idx, &e0, &e1);
+    const size_t blockvals = (size_t)b.s * b.nd * b.r;
+    const size_t v0 = (size_t)e0 * blockvals, v1 = (size_t)e1 * blockvals;
+    int k;
+    double accd[kEngRows];
+    if (ph == kPhResid) {
+      k = 1;
+      double a = 0.0;
+      for (size_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) a = fma(b.R[v], b.R[v], a);
+      accd[0] = a;
+    } else {
+      const int j = L.ctl[item.slot].j;
+      k = j + 2;
+      const float* w = b.V + (size_t)(j + 1) * b.L;
+      float acc[kEngRows];
+#pragma unroll
+      for (int i = 0; i < kEngRows; ++i) acc[i] = 0.f;
+      for (size_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        const float wv = w[v];
+#pragma unroll
+        for (int i = 0; i < kEngRows; ++i)
+          if (i < k) acc[i] = fmaf(b.V[(size_t)i * b.L + v], wv, acc[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < kEngRows; ++i) accd[i] = (double)acc[i];
+    }
+#pragma unroll
+    for (int i = 0; i < kEngRows; ++i) {
+      if (i < k) {
+        double v = accd[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wid][i] = v;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < k) {
+      double v = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[q][threadIdx.x];
+      L.partials[(size_t)it * kEngRows + threadIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Givens column update and the end-of-cycle test (lane 0 of the slot's warp).
+__device__ void finish_column(SlotCtl& c, const SlotBuf& b, OpArgs<float>& a32, double r2) {
+  const int j = c.j;
+  if (!isfinite(r2)) {
+    c.status = STDG_ERR_NAN;
+    c.phase = kPhDone;
+    c.upd = kUpdNone;
+    return;
+  }
+  const double hn = sqrt(r2 > 0.0 ? r2 : 0.0);
+  double* H = c.H;
+  for (int i = 0; i < j; ++i) {
+    const double t0 = c.cs[i] * H[i * kEngRows + j] + c.sn[i] * H[(i + 1) * kEngRows + j];
+    H[(i + 1) * kEngRows + j] = -c.sn[i] * H[i * kEngRows + j] + c.cs[i] * H[(i + 1) * kEngRows + j];
+    H[i * kEngRows + j] = t0;
+  }
+  double den = hypot(H[j * kEngRows + j], hn);
+  if (den == 0.0) den = 1e-300;
+  c.cs[j] = H[j * kEngRows + j] / den;
+  c.sn[j] = hn / den;
+  H[j * kEngRows + j] = den;
+  c.g[j + 1] = -c.sn[j] * c.g[j];
+  c.g[j] = c.cs[j] * c.g[j];
+  c.gmres_its += 1;
+  c.sig[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+  const bool done = fabs(c.g[j + 1]) <= c.tol || j + 1 >= c.m || hn <= 1e-300 * c.beta;
+  if (done) {
+    // y = H^-1 g (upper triangular), U += sum_i y_i z_i
+    const int kd = j + 1;
+    double y[kEngRows];
+    for (int i = kd - 1; i >= 0; --i) {
+      double acc = c.g[i];
+      for (int q = i + 1; q < kd; ++q) acc -= H[i * kEngRows + q] * y[q];
+      y[i] = acc / H[i * kEngRows + i];
+    }
+    for (int i = 0; i < kd; ++i) c.coef[i] = y[i];
+    c.upd = kUpdSolve;
+    c.upd_k = kd;
+    c.newton_its += 1;
+    c.phase = kPhResid;
+  } else {
+    // w -= V c (coefficients of this pass), z_{j+1} = P^-1 (w / |w|)
+    c.upd = kUpdGSZ;
+    c.upd_row = j + 1;
+    c.upd_k = j + 1;
+    c.zscale = c.sig[j + 1];
+    c.j = j + 1;
+    c.phase = kPhArnoldi;
+    a32.v = b.Z + (size_t)(j + 1) * b.L;
+    a32.out = b.V + (size_t)(j + 2) * b.L;
+  }
+}
+
+// One warp per active slot.
+__global__ void __launch_bounds__(kEngThreads) eng_control_kernel(const __grid_constant__ EngLaunch L) {
+  __shared__ double sp[kEngThreads / 32][kEngRows];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (g >= L.n_active) return;
+  const int slot = L.active[g];
+  SlotCtl& c = L.ctl[slot];
+  const SlotBuf& b = L.buf[slot];
+  const int ph = c.phase;
+  if (ph != kPhResid && ph != kPhArnoldi && ph != kPhReorth) {
+    if (lane == 0) c.upd = kUpdNone;
+    return;
+  }
+  const int k = ph == kPhResid ? 1 : c.j + 2;
+  for (int i = 0; i < k; ++i) {
+    double p = 0.0;
+    for (int q = lane; q < b.nitems; q += 32) p += L.partials[(size_t)(b.item0 + q) * kEngRows + i];
+    p = warp_sum_xor(p);
+    if (lane == 0) sp[wid][i] = p;
+  }
+  __syncwarp();
+  if (lane != 0) return;
+  const double* P = sp[wid];
+  OpArgs<float>& a32 = L.a32[slot];
+  if (ph == kPhResid) {
+    const double res = sqrt(P[0]);
+    c.resid_evals += 1;
+    c.res = res;
+    if (c.resid_evals == 1) {
+      c.res0 = res;
+      c.target = fmax(c.rtol * res, c.atol);
+    }
+    if (!isfinite(res)) {
+      c.status = STDG_ERR_NAN;
+      c.phase = kPhDone;
+      c.upd = kUpdNone;
+    } else if (res <= c.target) {
+      c.status = STDG_OK;
+      c.phase = kPhDone;
+      c.upd = kUpdExtract;
+    } else if (c.newton_its >= c.newton_maxit) {
+      c.status = STDG_ERR_NOT_CONVERGED;
+      c.phase = kPhDone;
+      c.upd = kUpdExtract;
+    } else {
+      c.beta = res;
+      c.tol = c.gmres_rtol * res;
+      c.sig[0] = -1.0 / res;  // V_0 holds R, v_0 = -R / |R|
+      for (int i = 0; i <= kEngRows; ++i) c.g[i] = 0.0;
+      c.g[0] = res;
+      c.j = 0;
+      c.upd = kUpdInit;
+      c.zscale = c.sig[0];
+      c.phase = kPhArnoldi;
+      a32.v = b.Z;
+      a32.out = b.V + b.L;
+    }
+    return;
+  }
+  const int j = c.j;
+  double* H = c.H;
+  if (ph == kPhArnoldi) {
+    c.jv_evals += 1;
+    const double w2 = P[j + 1];
+    double h2 = 0.0;
+    for (int i = 0; i <= j; ++i) {
+      const double h = c.sig[i] * P[i];
+      H[i * kEngRows + j] = h;
+      h2 += h * h;
+      c.coef[i] = c.sig[i] * h;
+    }
+    const double r2 = w2 - h2;
+    if (!(r2 > 0.01 * w2) && isfinite(r2)) {
+      // strong cancellation: apply this projection, then project once more
+      c.phase = kPhReorth;
+      c.upd = kUpdGS;
+      c.upd_row = j + 1;
+      c.upd_k = j + 1;
+      return;
+    }
+    finish_column(c, b, a32, r2);
+  } else {
+    double e2 = 0.0;
+    for (int i = 0; i <= j; ++i) {
+      const double h = c.sig[i] * P[i];
+      H[i * kEngRows + j] += h;
+      e2 += h * h;
+      c.coef[i] = c.sig[i] * h;
+    }
+    finish_column(c, b, a32, P[j + 1] - e2);
+  }
+}
+
+// Vector update of one tick.  Thread per (element, value q of a temporal
+// node's block) of the chunk; the s temporal values of q are handled together
+// so that z = (P^-1 (x) I_r) x is formed in registers.
+__global__ void __launch_bounds__(kEngThreads) eng_update_kernel(const __grid_constant__ EngLaunch L) {
+  __shared__ float cf[kEngRows];
+  const int n = *L.n_chunk_items;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const EngItem item = L.chunk_items[it];
+    const SlotCtl& c = L.ctl[item.slot];
+    const int mode = c.upd;
+    if (mode == kUpdNone) continue;
+    const SlotBuf b = L.buf[item.slot];
+    const int k = c.upd_k;
+    if ((mode == kUpdGS || mode == kUpdGSZ || mode == kUpdSolve) && threadIdx.x < k)
+      cf[threadIdx.x] = (float)c.coef[threadIdx.x];
+    __syncthreads();
+    const int row = c.upd_row;
+    const float zs = (float)c.zscale;
+    long long e0, e1;
+    chunk_range(b, item.idx, &e0, &e1);
+    const int s = b.s, nd = b.nd, r = b.r;
+    const int tnode = nd * r;
+    const size_t total = (size_t)(e1 - e0) * tnode;
+    for (size_t t = threadIdx.x; t < total; t += blockDim.x) {
+      const size_t e = (size_t)e0 + t / tnode;
+      const int q = (int)(t % tnode);
+      const int node = q / r;
+      const size_t base = e * s * tnode + q;  // (e, m = 0, q)
+      float x[kMaxS];
+      bool apply_z = false;
+      float* zout = nullptr;
+      if (mode == kUpdInit) {
+        for (int m = 0; m < s; ++m) {
+          const float v = (float)b.R[base + (size_t)m * tnode];
+          b.V[base + (size_t)m * tnode] = v;
+          x[m] = zs * v;
+        }
+        apply_z = true;
+        zout = b.Z;
+      } else if (mode == kUpdGS || mode == kUpdGSZ) {
+        float* w = b.V + (size_t)row * b.L;
+        for (int m = 0; m < s; ++m) {
+          const size_t o = base + (size_t)m * tnode;
+          float acc = w[o];
+          for (int i = 0; i < k; ++i) acc = fmaf(-cf[i], b.V[(size_t)i * b.L + o], acc);
+          w[o] = acc;
+          x[m] = zs * acc;
+        }
+        apply_z = mode == kUpdGSZ;
+        zout = b.Z + (size_t)row * b.L;
+      } else if (mode == kUpdSolve) {
+        for (int m = 0; m < s; ++m) {
+          const size_t o = base + (size_t)m * tnode;
+          float acc = 0.f;
+          for (int i = 0; i < k; ++i) acc = fmaf(cf[i], b.Z[(size_t)i * b.L + o], acc);
+          const double u = b.U[o] + (double)acc;
+          b.U[o] = u;
+          b.U32[o] = (float)u;
+        }
+      } else if (mode == kUpdExtract) {
+        b.uprev[e * tnode + q] = b.U[base + (size_t)(s - 1) * tnode];
+      }
+      if (apply_z) {
+        const float* P = b.Pinv + (e * s * s) * nd + node;
+        for (int m = 0; m < s; ++m) {
+          float z = 0.f;
+          for (int jj = 0; jj < s; ++jj) z = fmaf(P[(size_t)(m * s + jj) * nd], x[jj], z);
+          zout[base + (size_t)m * tnode] = z;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void eng_init_kernel(const SlotBuf b) {
+  const int tnode = b.nd * b.r;
+  const size_t total = (size_t)b.nelem * b.s * tnode;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+    const size_t e = idx / ((size_t)b.s * tnode);
+    const size_t q = idx % tnode;
+    const double u = b.uprev[e * tnode + q];
+    b.U[idx] = u;
+    b.U32[idx] = (float)u;
+  }
+}
+
+}  // namespace
+
+cudaError_t eng_generic_launch(const EngLaunch& L, cudaStream_t st) {
+  if (L.n_active <= 0) return cudaSuccess;
+  eng_dot_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
+  const int warps_per_block = kEngThreads / 32;
+  eng_control_kernel<<<(L.n_active + warps_per_block - 1) / warps_per_block, kEngThreads, 0, st>>>(L);
+  eng_update_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t eng_init_slot(const SlotBuf& b, cudaStream_t st) {
+  size_t total = (size_t)b.nelem * b.s * b.nd * b.r;
+  size_t blocks = (total + 255) / 256;
+  if (blocks > 2432) blocks = 2432;
+  eng_init_kernel<<<(unsigned)(blocks ? blocks : 1), 256, 0, st>>>(b);
+  return cudaGetLastError();
+}
+
+}  // namespace stdg

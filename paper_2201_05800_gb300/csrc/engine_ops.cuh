@@ -1,0 +1,83 @@
+// Physics-dependent kernels of the batched engine (engine.cuh): point-block
+// build and the two space-time operator passes (FP64 residual, FP32 exact
+// Jacobian-vector product), each walking the engine's work-item lists.
+#pragma once
+
+#include <type_traits>
+
+#include "engine.cuh"
+#include "operator.cuh"
+#include "precond.cuh"
+
+namespace stdg {
+
+template <class T> __device__ __forceinline__ const OpArgs<T>* eng_args(const EngLaunch& L, int slot);
+template <> __device__ __forceinline__ const OpArgs<double>* eng_args<double>(const EngLaunch& L, int slot) {
+  return L.a64 + slot;
+}
+template <> __device__ __forceinline__ const OpArgs<float>* eng_args<float>(const EngLaunch& L, int slot) {
+  return L.a32 + slot;
+}
+
+// Operator tiles of the slots in phase `want`; the slot's arguments are copied
+// to shared memory first (they change from tick to tick).
+template <int DIM, int EQ, class T, int MODE>
+__global__ void __launch_bounds__(256) eng_op_kernel(const __grid_constant__ EngLaunch L, int want) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) OpArgs<T> ks;
+  static_assert(sizeof(OpArgs<T>) % 4 == 0, "OpArgs copied as 32-bit words");
+  const int n = *L.n_op_items;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const EngItem item = L.op_items[it];
+    if (L.ctl[item.slot].phase != want) continue;
+    const OpArgs<T>* ga = eng_args<T>(L, item.slot);
+    // one item list serves both precisions: skip tiles beyond this precision's tile count
+    if ((long long)item.idx * ga->epb >= ga->nelem) continue;
+    const unsigned* src = reinterpret_cast<const unsigned*>(ga);
+    unsigned* dst = reinterpret_cast<unsigned*>(&ks);
+    for (int i = threadIdx.x; i < (int)(sizeof(OpArgs<T>) / 4); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    st_operator_tile<DIM, EQ, T, MODE, kMaxN, kMaxS, false>(ks, item.idx, smem_raw);
+  }
+}
+
+template <int DIM, int EQ>
+__global__ void __launch_bounds__(128) eng_build_kernel(const __grid_constant__ EngLaunch L) {
+  const int n = *L.n_chunk_items;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const EngItem item = L.chunk_items[it];
+    if (L.ctl[item.slot].phase != kPhResid) continue;
+    const SlotBuf& b = L.buf[item.slot];
+    const long long e0 = (long long)item.idx * b.chunk_elems;
+    const long long e1 = e0 + b.chunk_elems < b.nelem ? e0 + b.chunk_elems : b.nelem;
+    for (long long idx = e0 * b.nd + threadIdx.x; idx < e1 * b.nd; idx += blockDim.x)
+      pb_build_node<DIM, EQ, float>(L.a64[item.slot], b.U, b.Pinv, idx);
+  }
+}
+
+template <class K>
+inline cudaError_t eng_smem_attr(K kern, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int DIM, int EQ>
+cudaError_t eng_physics_inst(const EngLaunch& L, cudaStream_t st) {
+  if (L.n_active <= 0) return cudaSuccess;
+  eng_build_kernel<DIM, EQ><<<L.chunk_grid, 128, 0, st>>>(L);
+  auto k64 = eng_op_kernel<DIM, EQ, double, kModeResidual>;
+  auto k32 = eng_op_kernel<DIM, EQ, float, kModeJvExact>;
+  cudaError_t e = eng_smem_attr(k64, L.op_smem64);
+  if (e != cudaSuccess) return e;
+  e = eng_smem_attr(k32, L.op_smem32);
+  if (e != cudaSuccess) return e;
+  k64<<<L.op_grid, 256, L.op_smem64, st>>>(L, kPhResid);
+  k32<<<L.op_grid, 256, L.op_smem32, st>>>(L, kPhArnoldi);
+  return cudaGetLastError();
+}
+
+cudaError_t eng_physics_euler2(const EngLaunch& L, cudaStream_t st);
+cudaError_t eng_physics_burgers2(const EngLaunch& L, cudaStream_t st);
+cudaError_t eng_physics_advection(int dim, const EngLaunch& L, cudaStream_t st);
+
+}  // namespace stdg

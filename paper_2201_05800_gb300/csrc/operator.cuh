@@ -70,9 +70,12 @@ __host__ __device__ inline size_t op_smem_bytes(int n, int s, int epb) {
   return b;
 }
 
-// NPX/NTX: compile-time n and s when FIXED, else upper bounds (runtime n, s).
+// One CTA's work: elements [tile * epb, tile * epb + epb) of the slab described
+// by k, with the CTA's dynamic shared memory.  NPX/NTX: compile-time n and s
+// when FIXED, else upper bounds (runtime n, s).  Ends with a __syncthreads, so
+// a CTA may call it again for another tile.
 template <int DIM, int EQ, class T, int MODE, int NPX, int NTX, bool FIXED>
-__global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant__ OpArgs<T> k) {
+__device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long tile, unsigned char* smem_raw) {
   using P = Phys<EQ, DIM>;
   constexpr int R = P::R;
   using V = typename std::conditional<MODE == kModeJvExact, Dual<T>, T>::type;
@@ -84,11 +87,10 @@ __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant_
   const int nf = nd / n;  // nodes on one face
   const int epb = k.epb;
 
-  const long long e0 = (long long)blockIdx.x * epb;
+  const long long e0 = tile * epb;
   const int nel = (int)((k.nelem - e0) < epb ? (k.nelem - e0) : epb);
   const int tid = threadIdx.x, nth = blockDim.x;
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);                             // [epb][R][ndp] state of node m
   T* sv = su + (size_t)epb * R * ndp;                                  // [epb][R][ndp] direction (exact)
   V* sf = reinterpret_cast<V*>(MODE == kModeJvExact ? sv + (size_t)epb * R * ndp : sv);  // [epb][DIM][R][ndp]
@@ -295,6 +297,12 @@ __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant_
     }
     __syncthreads();
   }
+}
+
+template <int DIM, int EQ, class T, int MODE, int NPX, int NTX, bool FIXED>
+__global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant__ OpArgs<T> k) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  st_operator_tile<DIM, EQ, T, MODE, NPX, NTX, FIXED>(k, blockIdx.x, smem_raw);
 }
 
 }  // namespace stdg

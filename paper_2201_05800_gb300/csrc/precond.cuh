@@ -24,6 +24,81 @@
 
 namespace stdg {
 
+// One (element, spatial node) idx = e * nd + node:  sigma_{I,m} from the wave speeds
+// lambda = max(|v_a| + c) over the two traces of every face through I, then
+// P_I by Gauss-Jordan elimination with partial pivoting (s <= 5).
+template <int DIM, int EQ, class TP>
+__device__ __forceinline__ void pb_build_node(const OpArgs<double>& k, const double* __restrict__ U,
+                                              TP* __restrict__ Pinv, long long idx) {
+  using P = Phys<EQ, DIM>;
+  constexpr int R = P::R;
+  const int n = k.n, s = k.s, nd = k.nd;
+  const long long e = idx / nd;
+  const int node = (int)(idx - e * nd);
+  const int strides[3] = {1, n, n * n};
+  const int ia[3] = {node % n, (node / n) % n, node / (n * n)};
+  const long long ec[3] = {e % k.K[0], (e / k.K[0]) % k.K[1], e / ((long long)k.K[0] * k.K[1])};
+  double sig[kMaxS];
+  for (int m = 0; m < s; ++m) {
+    double uo[R];
+    const size_t go = (((size_t)e * s + m) * nd + node) * R;
+#pragma unroll
+    for (int c = 0; c < R; ++c) uo[c] = U[go + c];
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const bool up = ia[a] == n - 1, lo = ia[a] == 0;
+      if (!up && !lo) continue;
+      long long en[3] = {ec[0], ec[1], ec[2]};
+      en[a] += up ? 1 : -1;
+      if (en[a] < 0) en[a] += k.K[a];
+      if (en[a] >= k.K[a]) en[a] -= k.K[a];
+      const long long enb = (en[2] * k.K[1] + en[1]) * k.K[0] + en[0];
+      const int nb_node = node + ((up ? 0 : n - 1) - ia[a]) * strides[a];
+      const size_t gn = (((size_t)enb * s + m) * nd + nb_node) * R;
+      double un[R];
+#pragma unroll
+      for (int c = 0; c < R; ++c) un[c] = U[gn + c];
+      const double lo_s = P::template speed<double, double>(uo, a, k);
+      const double nb_s = P::template speed<double, double>(un, a, k);
+      acc += 0.5 * k.ginv[a] * k.winv_end * (lo_s >= nb_s ? lo_s : nb_s);
+    }
+    sig[m] = acc;
+  }
+  // augmented [P | I], row m = temporal node m
+  double A[kMaxS][2 * kMaxS];
+  for (int m = 0; m < s; ++m) {
+    for (int j = 0; j < s; ++j) {
+      double v = k.C[j][m];
+      if (m == j) v -= k.half_dt * k.omega[m] * sig[m];
+      if (m == s - 1 && j == s - 1) v -= 1.0;
+      A[m][j] = v;
+      A[m][s + j] = (m == j) ? 1.0 : 0.0;
+    }
+  }
+  for (int col = 0; col < s; ++col) {
+    int piv = col;
+    for (int q = col + 1; q < s; ++q)
+      if (fabs(A[q][col]) > fabs(A[piv][col])) piv = q;
+    if (piv != col)
+      for (int j = 0; j < 2 * s; ++j) {
+        const double t = A[col][j];
+        A[col][j] = A[piv][j];
+        A[piv][j] = t;
+      }
+    const double inv = 1.0 / A[col][col];
+    for (int j = 0; j < 2 * s; ++j) A[col][j] *= inv;
+    for (int q = 0; q < s; ++q) {
+      if (q == col) continue;
+      const double f = A[q][col];
+      if (f != 0.0)
+        for (int j = 0; j < 2 * s; ++j) A[q][j] -= f * A[col][j];
+    }
+  }
+  for (int m = 0; m < s; ++m)
+    for (int j = 0; j < s; ++j) Pinv[(((size_t)e * s + m) * s + j) * nd + node] = (TP)A[m][s + j];
+}
+
 // Pinv of every spatial node from the wave speeds of the slab U (FP64 layout
 // [e][m][node][c]); Pinv in TP (double or float).
 template <class TP>

@@ -274,6 +274,131 @@ class Context:
         return r.value
 
 
+class stdg_batch_desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("equation", ctypes.c_int), ("max_slots", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_size_t)]
+
+
+_BATCH_SIGS = {
+    "stdg_batch_create": (ctypes.c_int, [ctypes.POINTER(stdg_batch_desc), _P, ctypes.POINTER(_P)]),
+    "stdg_batch_destroy": (ctypes.c_int, [_P]),
+    "stdg_batch_add": (ctypes.c_int, [_P, ctypes.POINTER(stdg_config_desc), _P, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "stdg_batch_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "stdg_batch_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "stdg_batch_query": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(stdg_slab_stats)]),
+    "stdg_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
+    "stdg_batch_get_slab": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
+    "stdg_batch_remove": (ctypes.c_int, [_P, ctypes.c_int]),
+    "stdg_batch_slot_bytes": (ctypes.c_size_t, [_P, ctypes.POINTER(stdg_config_desc)]),
+    "stdg_batch_free_bytes": (ctypes.c_size_t, [_P]),
+    "stdg_batch_last_error": (ctypes.c_char_p, [_P]),
+}
+_SIGS.update(_BATCH_SIGS)
+
+
+class Batch:
+    """Owns one stdg_batch (batched device-driven slab solves).  Methods mirror stdg_batch_*."""
+
+    def __init__(self, dim, equation, max_slots, hbm_budget_bytes, stream=None):
+        lib = load()
+        self._lib = lib
+        self.desc = stdg_batch_desc(dim, equation, max_slots, hbm_budget_bytes)
+        h = _P()
+        st = lib.stdg_batch_create(ctypes.byref(self.desc), ctypes.c_void_p(stream) if stream is not None else None,
+                                   ctypes.byref(h))
+        if st != 0:
+            raise StdgError(st, "stdg_batch_create failed")
+        self._h = h
+        self._descs = {}
+
+    def _check(self, st):
+        if st != 0:
+            raise StdgError(st, (self._lib.stdg_batch_last_error(self._h) or b"").decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.stdg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def slot_bytes(self, desc):
+        return self._lib.stdg_batch_slot_bytes(self._h, ctypes.byref(desc))
+
+    def free_bytes(self):
+        return self._lib.stdg_batch_free_bytes(self._h)
+
+    def add(self, desc, u0):
+        """Admit one problem; returns the slot id (raises StdgError STDG_ERR_OOM when full)."""
+        p, kind = _ptr(u0, None)
+        slot = ctypes.c_int(-1)
+        self._check(self._lib.stdg_batch_add(self._h, ctypes.byref(desc), p, kind, ctypes.byref(slot)))
+        self._descs[slot.value] = desc
+        return slot.value
+
+    def try_add(self, desc, u0):
+        """Like add, but returns None when the arena or the slot table is full."""
+        try:
+            return self.add(desc, u0)
+        except StdgError as e:
+            if e.status == 2:
+                return None
+            raise
+
+    def step(self, ticks=1):
+        w = ctypes.c_int(0)
+        self._check(self._lib.stdg_batch_step(self._h, ticks, ctypes.byref(w)))
+        return w.value
+
+    def run(self, max_ticks=100000):
+        w = ctypes.c_int(0)
+        self._check(self._lib.stdg_batch_run(self._h, max_ticks, ctypes.byref(w)))
+        return w.value
+
+    def query(self, slot):
+        done, status = ctypes.c_int(0), ctypes.c_int(0)
+        stats = stdg_slab_stats()
+        self._check(self._lib.stdg_batch_query(self._h, slot, ctypes.byref(done), ctypes.byref(status),
+                                               ctypes.byref(stats)))
+        return bool(done.value), status.value, stats.as_dict()
+
+    def _len(self, slot, slab):
+        d = self._descs[slot]
+        r = d.dim + 2 if d.equation == EULER else 1
+        n = r
+        for a in range(d.dim):
+            n *= d.cells[a] * (d.N + 1)
+        return n * (d.s if slab else 1)
+
+    def get_state(self, slot, out=None):
+        out = np.empty(self._len(slot, False)) if out is None else out
+        p, kind = _ptr(out, None)
+        self._check(self._lib.stdg_batch_get_state(self._h, slot, p, kind))
+        return out
+
+    def get_slab(self, slot, out=None):
+        out = np.empty(self._len(slot, True)) if out is None else out
+        p, kind = _ptr(out, None)
+        self._check(self._lib.stdg_batch_get_slab(self._h, slot, p, kind))
+        return out
+
+    def remove(self, slot):
+        self._check(self._lib.stdg_batch_remove(self._h, slot))
+        self._descs.pop(slot, None)
+
+
 def version():
     return load().stdg_version().decode()
 

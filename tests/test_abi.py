@@ -75,3 +75,15 @@ def test_null_arguments(lib):
     assert lib.stdg_create(None, None, None) == 1
     assert lib.stdg_destroy(None) == 1
     assert lib.stdg_state_len(None) == 0
+
+
+def test_batch_validation_without_gpu(lib):
+    from paper_2201_05800_gb300 import stdg
+    h = ctypes.c_void_p()
+    assert lib.stdg_batch_create(None, None, ctypes.byref(h)) == 1
+    for bad in [stdg.stdg_batch_desc(3, stdg.EULER, 4, 1 << 20), stdg.stdg_batch_desc(2, stdg.EULER, 0, 1 << 20),
+                stdg.stdg_batch_desc(2, stdg.EULER, 4, 0), stdg.stdg_batch_desc(1, stdg.BURGERS, 4, 1 << 20)]:
+        assert lib.stdg_batch_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
+        assert not h.value
+    assert lib.stdg_batch_destroy(None) == 1
+    assert lib.stdg_batch_free_bytes(None) == 0

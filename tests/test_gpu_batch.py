@@ -1,0 +1,139 @@
+"""Batched device-driven slab solves (stdg_batch_*) through the C ABI.
+
+* Every slot of a mixed batch (different grids, N, s, dt) reaches the oracle's
+  FP64 slab solution: 1e-11 (relative LGL-weighted L2) when iterated to FP64
+  tolerances (the FP64 residual refines the FP32 Krylov solves), 1e-8 at the
+  workload tolerances (Newton rtol 1e-10, GMRES rtol 1e-3).
+* A slot's result is bitwise the same alone and in a mix of other slots.
+* Admission by memory: a full arena refuses a slot with STDG_ERR_OOM; removing
+  a finished slot makes room.
+"""
+import numpy as np
+import pytest
+
+from helpers import Problem, rel_lgl
+from oracle import physics, stdg as ost
+from paper_2201_05800_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TIGHT = dict(newton_rtol=1e-14, newton_atol=1e-13, newton_maxit=30, gmres_m=30, gmres_rtol=1e-4)
+WORK = dict(newton_rtol=1e-10, newton_atol=0.0, newton_maxit=30, gmres_m=30, gmres_rtol=1e-3)
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2201_05800_gb300 import build, stdg
+    build.build()
+    stdg.load()
+    return stdg
+
+
+def _vortex(cells, N, s, box=10.0):
+    prob = Problem(dim=2, cells=cells, N=N, s=s, eq="euler", dt=1.0, lo=(0.0, 0.0), hi=(box, box))
+    X = prob.grid.coordinates()
+    u0 = inputs.isentropic_vortex(X[0], X[1], center=(box / 2, box / 2))
+    lam = max(np.max(physics.wave_speed("euler", u0, a, prob.grid.params)) for a in range(2))
+    prob.dt = 0.5 * min(prob.grid.h) / lam
+    return prob, u0
+
+
+def _advection(cells, N, s, dt):
+    prob = Problem(dim=1, cells=cells, N=N, s=s, eq="advection", dt=dt, adv=(1.0,))
+    return prob, inputs.sine(prob.grid.coordinates()[0])
+
+
+def _oracle(prob, u0):
+    return ost.solve_slab_newton_gmres("stdg", prob.F, u0, prob.dt, prob.s, rtol=1e-14, atol=1e-13,
+                                       gmres_tol=1e-11, gmres_m=40)
+
+
+# (cells, N, s) of the 2D vortex on [0,10]^2 at CFL 0.5.  The N = 6 grid is stiff (nodal CFL
+# number ~ 12): its residual stalls near 1e-13 (FP64 rounding), so it is iterated to the
+# workload tolerances only.
+EULER_MIX = [((4, 4), 3, 3), ((6, 5), 4, 4), ((3, 4), 2, 2), ((5, 3), 5, 5), ((4, 4), 6, 3)]
+
+
+@pytest.mark.parametrize("tol,bound,cases", [(TIGHT, 1e-11, EULER_MIX[:4]), (WORK, 1e-8, EULER_MIX)])
+def test_euler_mix_matches_oracle(S, tol, bound, cases):
+    probs = [_vortex(*c) for c in cases]
+    with S.Batch(2, S.EULER, 16, 256 << 20) as B:
+        slots = [B.add(p.config(**tol), np.ascontiguousarray(u0).ravel()) for p, u0 in probs]
+        assert B.run(20000) == 0
+        for (p, u0), slot in zip(probs, slots):
+            done, status, st = B.query(slot)
+            assert done and status == 0, (status, st)
+            U = p.from_ext(B.get_slab(slot))
+            err = rel_lgl(p, U, _oracle(p, u0))
+            assert err <= bound, (p.cells, p.N, p.s, err, st)
+            u1 = B.get_state(slot).reshape(u0.shape)
+            assert np.array_equal(u1, U[p.s - 1])
+
+
+def test_advection_mix_matches_oracle(S):
+    cases = [((16,), 3, 3, 0.01), ((7,), 5, 2, 0.03), ((9,), 2, 5, 0.05), ((1,), 4, 4, 0.02)]
+    probs = [_advection(*c) for c in cases]
+    with S.Batch(1, S.ADVECTION, 8, 64 << 20) as B:
+        slots = [B.add(p.config(**TIGHT), np.ascontiguousarray(u0).ravel()) for p, u0 in probs]
+        B.run(20000)
+        for (p, u0), slot in zip(probs, slots):
+            done, status, st = B.query(slot)
+            assert done and status == 0
+            U = p.from_ext(B.get_slab(slot))
+            assert rel_lgl(p, U, _oracle(p, u0)) <= 1e-11
+
+
+def test_alone_equals_in_mix_bitwise(S):
+    probs = [_vortex(*c) for c in EULER_MIX]
+    target = 1
+    p, u0 = probs[target]
+    with S.Batch(2, S.EULER, 4, 64 << 20) as B:
+        s_alone = B.add(p.config(**WORK), np.ascontiguousarray(u0).ravel())
+        B.run(20000)
+        alone = B.get_slab(s_alone)
+        st_alone = B.query(s_alone)[2]
+    with S.Batch(2, S.EULER, 16, 256 << 20) as B:
+        # others admitted before and after, and one admitted while the target is running
+        first = [B.add(q.config(**WORK), np.ascontiguousarray(v).ravel()) for q, v in probs[:1]]
+        s_mix = B.add(p.config(**WORK), np.ascontiguousarray(u0).ravel())
+        B.step(5)
+        late = [B.add(q.config(**WORK), np.ascontiguousarray(v).ravel()) for q, v in probs[2:]]
+        B.run(20000)
+        mixed = B.get_slab(s_mix)
+        st_mix = B.query(s_mix)[2]
+        assert all(B.query(sl)[0] for sl in first + late)
+    assert np.array_equal(alone, mixed)
+    assert st_alone == st_mix
+
+
+def test_admission_by_memory(S):
+    p, u0 = _vortex((8, 8), 4, 4)
+    with S.Batch(2, S.EULER, 4, 1 << 20) as probe:
+        need = probe.slot_bytes(p.config(**WORK))
+    with S.Batch(2, S.EULER, 4, need + need // 2) as B:
+        a = B.add(p.config(**WORK), np.ascontiguousarray(u0).ravel())
+        assert B.try_add(p.config(**WORK), np.ascontiguousarray(u0).ravel()) is None
+        B.run(20000)
+        assert B.query(a)[0]
+        B.remove(a)
+        b = B.try_add(p.config(**WORK), np.ascontiguousarray(u0).ravel())
+        assert b is not None
+        B.run(20000)
+        assert B.query(b)[:2] == (True, 0)
+
+
+def test_failure_statuses(S):
+    p, u0 = _vortex((4, 4), 3, 3)
+    bad = np.ascontiguousarray(u0).ravel().copy()
+    bad[5] = np.nan
+    with S.Batch(2, S.EULER, 4, 64 << 20) as B:
+        s_nan = B.add(p.config(**WORK), bad)
+        s_cap = B.add(p.config(**dict(WORK, newton_rtol=1e-15, newton_maxit=1, gmres_rtol=0.5)),
+                      np.ascontiguousarray(u0).ravel())
+        s_ok = B.add(p.config(**WORK), np.ascontiguousarray(u0).ravel())
+        B.run(20000)
+        assert B.query(s_nan)[:2] == (True, 6)   # STDG_ERR_NAN
+        assert B.query(s_cap)[:2] == (True, 4)   # STDG_ERR_NOT_CONVERGED
+        assert B.query(s_ok)[:2] == (True, 0)
