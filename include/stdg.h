@@ -8,14 +8,18 @@
  * nonlinear system is Eq. DG_vs_RK:DG, solved by Jacobian-free Newton-Krylov
  * (Newton + restarted GMRES, Sec. 6.3 "Nonlinear solvers and preconditioning").
  *
- * Problem (Eq. general with F_v = 0, S = 0): d_t u + div F_c(u) = 0 on a
+ * Problem (Eq. general with S = 0): d_t u + div F_c(u) = div F_v on a
  * uniform periodic Cartesian grid (Sec. 3.1), with
  *   STDG_ADVECTION  u_t + a . grad u = 0              (r = 1)
  *   STDG_EULER      Euler equations, Eqs. eulereq/defu (r = d + 2,
  *                   u = (rho, rho v_1..rho v_d, E))
  *   STDG_BURGERS    u_t + div(u^2/2 (1,..,1)) = 0      (r = 1)
  * and the Rusanov (local Lax-Friedrichs) flux of Eq. flux:llf on every face
- * (exact upwind for advection).  Initial data are nodal values on the LGL
+ * (exact upwind for advection).  For the scalar equations a viscous flux
+ * F_v = nu grad u may be added (viscosity > 0): the symmetric interior penalty
+ * form with the numerical flux H_v^IP of Sec. 3.1, penalty eta (default
+ * 10 N^2, the paper's UFL choice) over h_e = h_a on faces normal to e_a, LGL
+ * quadrature on elements and faces.  Initial data are nodal values on the LGL
  * nodes (interpolation = the quadrature projection of Eq. ode).
  *
  * Discrete residual evaluated by the library (the reading that makes its
@@ -112,6 +116,8 @@ typedef struct {
   int gmres_maxit;          /* total inner iterations per Newton step, >= 1              */
   size_t hbm_budget_bytes;  /* 0 = unlimited; else create fails with STDG_ERR_OOM above  */
   int precond;              /* STDG_PRECOND_NONE | _TEMPORAL_MASS (default) | _POINT_BLOCK */
+  double viscosity;         /* nu >= 0: adds nu Laplace(u) (advection and Burgers only)  */
+  double penalty;           /* interior penalty eta; <= 0 means the paper's 10 N^2       */
 } stdg_config_desc;
 
 typedef struct {

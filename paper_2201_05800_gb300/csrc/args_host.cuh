@@ -10,9 +10,12 @@
 
 namespace stdg {
 
+// nu > 0: constants of the symmetric interior penalty form of -nu Laplace(u)
+// (F_v = nu grad u in Eq. general, H_v^IP of Sec. 3.1 with penalty eta,
+// eta <= 0 meaning the paper's 10 N^2, and h_e = h_a on faces normal to e_a).
 template <class T>
 inline void fill_op_args(OpArgs<T>& k, int dim, int n, int s, const int cells[3], const double h[3], double dt,
-                         double gamma, const double adv[3]) {
+                         double gamma, const double adv[3], double nu = 0.0, double eta = 0.0) {
   std::memset(&k, 0, sizeof(k));
   k.n = n;
   k.s = s;
@@ -46,6 +49,29 @@ inline void fill_op_args(OpArgs<T>& k, int dim, int n, int s, const int cells[3]
   for (int a = 0; a < 3; ++a) k.adv[a] = (T)adv[a];
   k.vscale = (T)1;
   for (int m = 0; m < s; ++m) k.inv_omega[m] = (T)(1.0 / om[m]);
+  k.nu = (T)nu;
+  if (nu > 0.0) {
+    const int N = n - 1;
+    const double pen_eta = eta > 0.0 ? eta : 10.0 * N * N;
+    for (int a = 0; a < dim; ++a) {
+      const double g = 2.0 / h[a];
+      const double sig = nu * pen_eta / h[a];
+      k.pen[a] = (T)sig;
+      for (int i = 0; i < n; ++i) {
+        for (int q = 0; q < n; ++q) k.vDW[a][i][q] = (T)(nu * g * (w[q] / w[i]) * D[q * n + i]);
+        k.vup[a][i] = (T)(0.5 * nu * g * g * D[N * n + i] / w[i]);
+        k.vlo[a][i] = (T)(0.5 * nu * g * g * D[0 * n + i] / w[i]);
+        // diagonal of B(e_i, e_i) / (J w_i) on one line (neighbours zero): volume part plus the
+        // face terms at the end nodes (penalty, averaged gradient, lifted jump)
+        double dg = 0.0;
+        for (int q = 0; q < n; ++q) dg += w[q] * D[q * n + i] * D[q * n + i];
+        dg *= nu * g * g / w[i];
+        if (i == N) dg += g * sig / w[N] - nu * g * g * D[N * n + N] / w[N];
+        if (i == 0) dg += g * sig / w[0] + nu * g * g * D[0] / w[0];
+        k.vdiag[a][i] = (T)dg;
+      }
+    }
+  }
 }
 
 }  // namespace stdg

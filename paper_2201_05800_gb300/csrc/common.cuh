@@ -47,6 +47,13 @@ struct OpArgs {
   T vscale;                // v is read as vscale * v (kModeJvFD / kModeJvExact)
   int lscale;              // Jv modes: rows of temporal node m divided by omega_m
   T inv_omega[kMaxS];      // 1 / omega_m
+  // symmetric interior penalty viscous term (scalar equations, nu > 0):
+  T nu;                    // viscosity (0: inviscid)
+  T pen[3];                // penalty sigma_a = nu eta / h_a
+  T vDW[3][kMaxN][kMaxN];  // nu (2/h_a) (w_k / w_i) D[k][i]: volume term, [a][i][k]
+  T vup[3][kMaxN];         // nu/2 (2/h_a)^2 D[N][i] / w_i: lift of the upper-face jump
+  T vlo[3][kMaxN];         // nu/2 (2/h_a)^2 D[0][i] / w_i: lift of the lower-face jump
+  T vdiag[3][kMaxN];       // diagonal of the viscous term of F per direction (preconditioner)
   const T* U;              // slab, [e][m][node][c]
   const T* v;              // direction, same layout
   const T* F0;             // F(U), same layout (kModeJvFD)

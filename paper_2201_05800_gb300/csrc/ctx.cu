@@ -162,7 +162,8 @@ int num_components(int eq, int dim) { return eq == STDG_EULER ? dim + 2 : 1; }
 
 template <class T>
 void fill_args(const stdg_ctx* c, OpArgs<T>& k) {
-  fill_op_args<T>(k, c->dim, c->n, c->s, c->d.cells, c->h, c->d.dt, c->d.gamma, c->d.adv_vel);
+  fill_op_args<T>(k, c->dim, c->n, c->s, c->d.cells, c->h, c->d.dt, c->d.gamma, c->d.adv_vel, c->d.viscosity,
+                  c->d.penalty);
 }
 
 stdg_status validate(const stdg_config_desc* d, std::string* why) {
@@ -185,6 +186,9 @@ stdg_status validate(const stdg_config_desc* d, std::string* why) {
   if (d->newton_maxit < 1 || d->gmres_maxit < 1) return bad("maxit must be >= 1");
   if (d->gmres_m < 1 || d->gmres_m > kMaxGmresM) return bad("gmres_m must be 1..31");
   if (!(d->newton_rtol >= 0) || !(d->newton_atol >= 0) || !(d->gmres_rtol > 0)) return bad("bad tolerance");
+  if (!(d->viscosity >= 0.0) || !std::isfinite(d->viscosity) || !std::isfinite(d->penalty))
+    return bad("viscosity must be finite and >= 0");
+  if (d->viscosity > 0.0 && d->equation == STDG_EULER) return bad("viscosity is supported for scalar equations");
   if (d->precond != STDG_PRECOND_NONE && d->precond != STDG_PRECOND_TEMPORAL_MASS &&
       d->precond != STDG_PRECOND_POINT_BLOCK)
     return bad("unknown precond");

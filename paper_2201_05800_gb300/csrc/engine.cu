@@ -160,6 +160,9 @@ stdg_status check_inst(const stdg_batch* b, const stdg_config_desc* d, std::stri
   if (d->gmres_m < 1 || d->gmres_m > kEngMaxM) return bad("gmres_m must be 1..31");
   if (d->newton_maxit < 1) return bad("newton_maxit must be >= 1");
   if (!(d->newton_rtol >= 0) || !(d->newton_atol >= 0) || !(d->gmres_rtol > 0)) return bad("bad tolerance");
+  if (!(d->viscosity >= 0.0) || !std::isfinite(d->viscosity) || !std::isfinite(d->penalty))
+    return bad("viscosity must be finite and >= 0");
+  if (d->viscosity > 0.0 && d->equation == STDG_EULER) return bad("viscosity is supported for scalar equations");
   return STDG_OK;
 }
 
@@ -446,8 +449,8 @@ stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* d, const doubl
   for (int a = 0; a < l.dim; ++a) h[a] = (d->hi[a] - d->lo[a]) / d->cells[a];
   OpArgs<double> k64;
   OpArgs<float> k32;
-  fill_op_args<double>(k64, l.dim, l.n, l.s, d->cells, h, d->dt, d->gamma, d->adv_vel);
-  fill_op_args<float>(k32, l.dim, l.n, l.s, d->cells, h, d->dt, d->gamma, d->adv_vel);
+  fill_op_args<double>(k64, l.dim, l.n, l.s, d->cells, h, d->dt, d->gamma, d->adv_vel, d->viscosity, d->penalty);
+  fill_op_args<float>(k32, l.dim, l.n, l.s, d->cells, h, d->dt, d->gamma, d->adv_vel, d->viscosity, d->penalty);
   k64.epb = hs.epb64;
   k64.U = sb.U;
   k64.uprev = sb.uprev;

@@ -67,6 +67,10 @@ __host__ __device__ inline size_t op_smem_bytes(int n, int s, int epb) {
   b += (size_t)epb * R * ndp * vbytes;                              // accumulators
   b += (size_t)epb * DIM * ndp * vbytes;                            // wave speeds
   b += (3 * kMaxN * kMaxN + kMaxS * kMaxS) * sizeof(T);             // scaled D per direction, C
+  if (R == 1) {                                                     // viscous term (scalar equations)
+    b += (size_t)epb * DIM * ndp * vbytes;                          // gradients
+    b += (size_t)epb * DIM * 2 * (nd / n) * vbytes;                 // face jumps
+  }
   return b;
 }
 
@@ -98,6 +102,9 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
   V* sl = sr + (size_t)epb * R * ndp;                                  // [epb][DIM][ndp] wave speeds
   T* sD = reinterpret_cast<T*>(sl + (size_t)epb * DIM * ndp);          // [3][kMaxN][kMaxN]  (2/h_a) D
   T* sC = sD + 3 * kMaxN * kMaxN;                                      // [kMaxS][kMaxS]  C
+  V* sq = reinterpret_cast<V*>(sC + kMaxS * kMaxS);                    // [epb][DIM][ndp] gradients (R == 1)
+  V* sjm = sq + (size_t)epb * DIM * ndp;                               // [epb][DIM][2][nf] face jumps (R == 1)
+  const bool visc = (R == 1) && k.nu != T(0);
   for (int i = tid; i < 3 * kMaxN * kMaxN; i += nth) {
     const int a = i / (kMaxN * kMaxN), q = i % (kMaxN * kMaxN);
     sD[i] = k.ginv[a] * k.D[q / kMaxN][q % kMaxN];
@@ -147,6 +154,26 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
 #pragma unroll
         for (int c = 0; c < R; ++c) sfe[(a * R + c) * ndp + node] = f[a][c];
       }
+      if constexpr (R == 1) {
+        if (visc) {
+          // gradient along each direction: (2/h_a) sum_j D[i_a][j] u along the line
+          const int idx[3] = {node % n, (node / n) % n, node / (n * n)};
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) {
+            const int base = node - idx[a] * strides[a];
+            const T* Da = sD + (a * kMaxN + idx[a]) * kMaxN;
+            V q = Lift<V, T>::from(T(0));
+#pragma unroll
+            for (int j = 0; j < NPX; ++j) {
+              if (FIXED || j < n) {
+                const size_t sj = ((size_t)el * R) * ndp + base + j * strides[a];
+                q = q + Da[j] * tile_state<MODE>(su[sj], MODE == kModeJvExact ? sv[sj] : T(0));
+              }
+            }
+            sq[((size_t)el * DIM + a) * ndp + node] = q;
+          }
+        }
+      }
     }
     __syncthreads();
     // ---- 2. volume term
@@ -167,6 +194,20 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
 #pragma unroll
           for (int j = 0; j < NPX; ++j) {
             if (FIXED || j < n) acc[c] = acc[c] - Da[j] * sfe[(a * R + c) * ndp + base + j * strides[a]];
+          }
+        }
+      }
+      if constexpr (R == 1) {
+        if (visc) {
+          // -nu sum_a (2/h_a) (1/w_i) sum_k w_k D[k][i] q_a(k)   (SIPG volume term)
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) {
+            const int ia = idx[a];
+            const int base = node - ia * strides[a];
+            const V* sqa = sq + ((size_t)el * DIM + a) * ndp;
+#pragma unroll
+            for (int j = 0; j < NPX; ++j)
+              if (FIXED || j < n) acc[0] = acc[0] - k.vDW[a][ia][j] * sqa[base + j * strides[a]];
           }
         }
       }
@@ -209,6 +250,7 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
         const size_t so = ((size_t)el * R) * ndp + own;
         const V* sfe = sf + (size_t)el * DIM * R * ndp;
         V um[R], up[R], fm[R], fp[R];
+        V qm = Lift<V, T>::from(T(0)), qp = Lift<V, T>::from(T(0));  // normal gradients (viscous)
 #pragma unroll
         for (int c = 0; c < R; ++c) {
           fm[c] = sfe[(a * R + c) * ndp + own];
@@ -225,6 +267,8 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
             up[c] = tile_state<MODE>(su[son + c * ndp], MODE == kModeJvExact ? sv[son + c * ndp] : T(0));
           }
           lp = sl[((size_t)eln * DIM + a) * ndp + nbr_node];
+          if constexpr (R == 1)
+            if (visc) qp = sq[((size_t)eln * DIM + a) * ndp + nbr_node];
         } else {
           const size_t gofs = ((size_t)en * s + m) * tnode + (size_t)nbr_node * R;
 #pragma unroll
@@ -232,7 +276,25 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
             up[c] = eval_state<MODE>(k.U[gofs + c], MODE == kModeResidual ? T(0) : k.vscale * k.v[gofs + c],
                                      k.eps);
           lp = P::flux_speed(up, a, fp, k);
+          if constexpr (R == 1) {
+            if (visc) {
+              // the neighbour's gradient at its face node from its line along e_a
+              const int ib = n - 1 - ia_own;
+              const T* Db = sD + (a * kMaxN + ib) * kMaxN;
+              const size_t lbase = ((size_t)en * s + m) * tnode + (size_t)(lo + hi * strides[a] * n) * R;
+#pragma unroll
+              for (int j = 0; j < NPX; ++j) {
+                if (FIXED || j < n) {
+                  const size_t gj = lbase + (size_t)j * strides[a] * R;
+                  qp = qp + Db[j] * eval_state<MODE>(k.U[gj], MODE == kModeResidual ? T(0) : k.vscale * k.v[gj],
+                                                     k.eps);
+                }
+              }
+            }
+          }
         }
+        if constexpr (R == 1)
+          if (visc) qm = sq[((size_t)el * DIM + a) * ndp + own];
         V* sre = sr + (size_t)el * R * ndp;
         if (side) {  // own element below the face: uL = u-, uR = u+
           const V lam = dmax(lm, lp);
@@ -243,6 +305,21 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
             sre[c * ndp + own] = sre[c * ndp + own] - g * (H - fm[c]);  // n = +e_a
             if (internal) srn[c * ndp + nbr_node] = srn[c * ndp + nbr_node] + g * (H - fp[c]);  // n = -e_a
           }
+          if constexpr (R == 1) {
+            if (visc) {
+              // jump [[u]] = uL - uR, average of nu grad u; the element below gets
+              // -(2/h)(1/w_N)(-nu {q} + sigma [[u]]), the element above -(2/h)(1/w_0)(nu {q} - sigma [[u]])
+              const V jmp = um[0] - up[0];
+              const V avg = T(0.5) * (qm + qp);
+              const V fb = k.nu * avg - k.pen[a] * jmp;
+              sre[own] = sre[own] + g * fb;
+              sjm[(((size_t)el * DIM + a) * 2 + 1) * nf + fidx] = jmp;
+              if (internal) {
+                srn[nbr_node] = srn[nbr_node] - g * fb;
+                sjm[(((size_t)eln * DIM + a) * 2 + 0) * nf + fidx] = jmp;
+              }
+            }
+          }
         } else {     // own element above the face: uL = u+, uR = u-
           const V lam = dmax(lp, lm);
 #pragma unroll
@@ -250,9 +327,39 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
             const V H = T(0.5) * (fp[c] + fm[c]) - T(0.5) * (lam * (um[c] - up[c]));
             sre[c * ndp + own] = sre[c * ndp + own] + g * (H - fm[c]);
           }
+          if constexpr (R == 1) {
+            if (visc) {
+              const V jmp = up[0] - um[0];
+              const V avg = T(0.5) * (qp + qm);
+              sre[own] = sre[own] - g * (k.nu * avg - k.pen[a] * jmp);
+              sjm[(((size_t)el * DIM + a) * 2 + 0) * nf + fidx] = jmp;
+            }
+          }
         }
       }
       __syncthreads();
+    }
+    if constexpr (R == 1) {
+      if (visc) {
+        // ---- 3b. lift of the face jumps along the normal lines (symmetry term of the
+        //          SIPG form): F_I += nu/2 (2/h_a)^2 (1/w_i) (D[N][i] [[u]]_up + D[0][i] [[u]]_lo)
+        for (int t = tid; t < nel * nd; t += nth) {
+          const int el = t / nd, node = t - el * nd;
+          const int idx[3] = {node % n, (node / n) % n, node / (n * n)};
+          V acc = sr[(size_t)el * ndp + node];
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) {
+            const int ia = idx[a];
+            const int lo = node % strides[a];
+            const int hi = node / (strides[a] * n);
+            const int fidx = lo + hi * strides[a];
+            const V* sja = sjm + ((size_t)el * DIM + a) * 2 * nf;
+            acc = acc + k.vup[a][ia] * sja[nf + fidx] + k.vlo[a][ia] * sja[fidx];
+          }
+          sr[(size_t)el * ndp + node] = acc;
+        }
+        __syncthreads();
+      }
     }
     // ---- 4. temporal coupling and output (coalesced: consecutive threads read and
     //         write consecutive values of the element's [node][c] block)

@@ -29,6 +29,10 @@ inline size_t operator_smem_bytes(int dim, int r, size_t tsize, int mode, int n,
   b += (size_t)epb * r * ndp * vbytes;
   b += (size_t)epb * dim * ndp * vbytes;
   b += (size_t)(3 * kMaxN * kMaxN + kMaxS * kMaxS) * tsize;
+  if (r == 1) {  // viscous term of the scalar equations: gradients and face jumps
+    b += (size_t)epb * dim * ndp * vbytes;
+    b += (size_t)epb * dim * 2 * (nd / n) * vbytes;
+  }
   return b;
 }
 

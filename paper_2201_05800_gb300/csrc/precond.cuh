@@ -13,6 +13,8 @@
 // by the SBP property, Eq. SBP; D[i][i] = 0 at the interior nodes).  So the
 // block is P_I (x) I_r with the s x s matrix
 //   P_I[m][j] = (D_tau^T M_tau)[m][j] - [m = j = s-1] - [m = j] dt/2 omega_m sigma_{I,m},
+// (with a viscous term, sigma also holds the diagonal of the interior-penalty
+// operator at I, which does not depend on U),
 // one per spatial node, the same for all r components.  Its inverse is stored
 // per node as Pinv[e][m][j][node] (node fastest, so that consecutive threads
 // of the apply kernel read consecutive addresses).
@@ -63,6 +65,9 @@ __device__ __forceinline__ void pb_build_node(const OpArgs<double>& k, const dou
       const double nb_s = P::template speed<double, double>(un, a, k);
       acc += 0.5 * k.ginv[a] * k.winv_end * (lo_s >= nb_s ? lo_s : nb_s);
     }
+    // viscous term: its diagonal is independent of U
+    if (k.nu != 0.0)
+      for (int a = 0; a < DIM; ++a) acc += k.vdiag[a][ia[a]];
     sig[m] = acc;
   }
   // augmented [P | I], row m = temporal node m

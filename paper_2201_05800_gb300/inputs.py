@@ -16,6 +16,8 @@ Initial conditions (Sec. 7 of the paper, with the readings stated per function):
 * ``density_wave``: rho = 1 + 0.2 sin(2 pi (x+y+z)), v = (1,1,1), p = 1 (in d
   dimensions: v = (1,..,1)); exact solution rho(x - t v).
 * ``burgers_fourier``: 8 random Fourier modes with amplitudes summing to 0.5.
+* ``burgers_instance``: the parameters of one instance of the batched viscous
+  Burgers workload (grid side, N, s, viscosity, data seed) drawn from its seed.
 """
 import math
 
@@ -93,3 +95,15 @@ def vortex_period_center(lo, hi):
 
 def log_uniform(rng, lo, hi):
     return math.exp(rng.uniform(math.log(lo), math.log(hi)))
+
+
+def burgers_instance(i, sides=(8, 16, 32, 64), N_range=(2, 6), s_range=(2, 5), nu_range=(1e-3, 1e-1)):
+    """Instance i of the batched 2D viscous Burgers workload on the periodic unit square:
+    seed 1000 + i draws the grid side (uniform over ``sides``), N and s (uniform integers in
+    the closed ranges), the viscosity (log-uniform) and the Fourier data seed."""
+    rng = np.random.default_rng(1000 + i)
+    side = int(sides[rng.integers(0, len(sides))])
+    N = int(rng.integers(N_range[0], N_range[1] + 1))
+    s = int(rng.integers(s_range[0], s_range[1] + 1))
+    nu = log_uniform(rng, *nu_range)
+    return {"side": side, "N": N, "s": s, "nu": nu, "seed": 1000 + i}

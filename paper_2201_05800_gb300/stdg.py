@@ -34,7 +34,8 @@ class stdg_config_desc(ctypes.Structure):
                 ("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double),
                 ("newton_maxit", ctypes.c_int), ("gmres_m", ctypes.c_int),
                 ("gmres_rtol", ctypes.c_double), ("gmres_maxit", ctypes.c_int),
-                ("hbm_budget_bytes", ctypes.c_size_t), ("precond", ctypes.c_int)]
+                ("hbm_budget_bytes", ctypes.c_size_t), ("precond", ctypes.c_int),
+                ("viscosity", ctypes.c_double), ("penalty", ctypes.c_double)]
 
 
 class stdg_slab_stats(ctypes.Structure):

@@ -21,12 +21,15 @@ EQ = {"advection": 0, "euler": 1, "burgers": 2}
 
 
 class Problem:
-    def __init__(self, dim, cells, N, s, eq, dt, lo=None, hi=None, adv=(1.0, 0.5, -0.75), gamma=1.4):
+    def __init__(self, dim, cells, N, s, eq, dt, lo=None, hi=None, adv=(1.0, 0.5, -0.75), gamma=1.4, nu=0.0):
         self.dim, self.cells, self.N, self.s, self.eq, self.dt = dim, tuple(cells), N, s, eq, dt
         self.lo = tuple(lo or (0.0,) * dim)
         self.hi = tuple(hi or (1.0,) * dim)
-        self.adv, self.gamma = tuple(adv), gamma
-        self.grid = dgsem.Grid(dim, cells, self.lo, self.hi, N, eq, {"adv_vel": self.adv, "gamma": gamma})
+        self.adv, self.gamma, self.nu = tuple(adv), gamma, nu
+        params = {"adv_vel": self.adv, "gamma": gamma}
+        if nu:
+            params["viscosity"] = nu
+        self.grid = dgsem.Grid(dim, cells, self.lo, self.hi, N, eq, params)
 
     def F(self, u):
         return dgsem.spatial_operator(self.grid, u)
@@ -35,7 +38,8 @@ class Problem:
         from paper_2201_05800_gb300 import stdg as S
         base = dict(dim=self.dim, cells=list(self.cells) + [1] * (3 - self.dim), lo=list(self.lo) + [0.0] * (3 - self.dim),
                     hi=list(self.hi) + [1.0] * (3 - self.dim), N=self.N, s=self.s, equation=EQ[self.eq],
-                    adv_vel=list(self.adv) + [0.0] * (3 - len(self.adv)), gamma=self.gamma, dt=self.dt)
+                    adv_vel=list(self.adv) + [0.0] * (3 - len(self.adv)), gamma=self.gamma, dt=self.dt,
+                    viscosity=self.nu)
         base.update(kw)
         return S.make_config(**base)
 
@@ -90,6 +94,13 @@ class Problem:
         Dmax = np.max(np.abs(g.D))
         spatial = sum((2.0 / g.h[a]) * (g.n * Dmax * fmax + (2 * fmax + lam * 2 * umax) / g.w[0])
                       for a in range(self.dim))
+        if self.nu:
+            # interior penalty terms: second differences, averaged gradients, penalised jumps
+            eta = 10.0 * self.N ** 2
+            wmin = np.min(g.w)
+            spatial += sum(self.nu * (2.0 / g.h[a]) ** 2 * (g.n * Dmax) ** 2 * umax * (1.0 + 2.0 / wmin)
+                           + (2.0 / g.h[a]) / wmin * (self.nu * eta / g.h[a]) * 2 * umax
+                           for a in range(self.dim))
         return (np.max(C.sum(axis=0)) + 2.0) * umax + 0.5 * self.dt * np.max(np.diag(M)) * spatial
 
 

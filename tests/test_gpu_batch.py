@@ -137,3 +137,30 @@ def test_failure_statuses(S):
         assert B.query(s_nan)[:2] == (True, 6)   # STDG_ERR_NAN
         assert B.query(s_cap)[:2] == (True, 4)   # STDG_ERR_NOT_CONVERGED
         assert B.query(s_ok)[:2] == (True, 0)
+
+
+def _burgers(i, max_side=16):
+    """Instance i of the batched viscous Burgers workload (grid side capped for the oracle),
+    dt = 0.5 h / max |u0| (CFL 0.5 on the initial data)."""
+    spec = inputs.burgers_instance(i, sides=tuple(x for x in (8, 16, 32, 64) if x <= max_side))
+    side = spec["side"]
+    prob = Problem(dim=2, cells=(side, side), N=spec["N"], s=spec["s"], eq="burgers", dt=1.0, nu=spec["nu"])
+    X = prob.grid.coordinates()
+    u0 = inputs.burgers_fourier(X[0], X[1], spec["seed"])
+    prob.dt = 0.5 * (1.0 / side) / np.max(np.abs(u0))
+    return prob, u0
+
+
+def test_viscous_burgers_mix_matches_oracle(S):
+    """Six instances of the batched viscous Burgers workload (8^2 and 16^2 grids) in one batch:
+    each slot within 1e-8 of the oracle at the workload tolerances."""
+    probs = [_burgers(i) for i in range(6)]
+    with S.Batch(2, S.BURGERS, 8, 256 << 20) as B:
+        slots = [B.add(p.config(**WORK), np.ascontiguousarray(u0).ravel()) for p, u0 in probs]
+        assert B.run(20000) == 0
+        for (p, u0), slot in zip(probs, slots):
+            done, status, st = B.query(slot)
+            assert done and status == 0, (status, st)
+            U = p.from_ext(B.get_slab(slot))
+            err = rel_lgl(p, U, _oracle(p, u0))
+            assert err <= 1e-8, (p.cells, p.N, p.s, p.nu, err, st)

@@ -41,6 +41,12 @@ CASES = {
     "euler3_fixed": dict(dim=3, cells=(3, 4, 2), N=3, s=3, eq="euler", dt=0.01),
     "euler3_generic": dict(dim=3, cells=(2, 3, 2), N=2, s=2, eq="euler", dt=0.02),
     "adv3": dict(dim=3, cells=(3, 2, 2), N=1, s=4, eq="advection", dt=0.05),
+    # viscous (symmetric interior penalty) terms, scalar equations
+    "adv1_visc": dict(dim=1, cells=(7,), N=3, s=3, eq="advection", dt=0.02, adv=(0.8,), nu=0.05),
+    "adv1_visc_one_elem": dict(dim=1, cells=(1,), N=4, s=2, eq="advection", dt=0.02, adv=(0.8,), nu=0.1),
+    "adv2_visc": dict(dim=2, cells=(5, 3), N=3, s=3, eq="advection", dt=0.01, nu=0.02),
+    "burgers2_visc": dict(dim=2, cells=(4, 6), N=5, s=2, eq="burgers", dt=0.01, nu=0.01),
+    "burgers2_visc_big": dict(dim=2, cells=(19, 14), N=2, s=4, eq="burgers", dt=0.01, nu=0.003),
 }
 
 
@@ -74,7 +80,8 @@ def test_exact_jv_parity(S, name):
     assert rel_lgl(prob, J, J_or) <= 1e-12
 
 
-@pytest.mark.parametrize("name", ["adv1_fixed", "euler1", "euler2_fixed_ragged", "euler3_fixed", "burgers2"])
+@pytest.mark.parametrize("name", ["adv1_fixed", "euler1", "euler2_fixed_ragged", "euler3_fixed", "burgers2",
+                                  "burgers2_visc"])
 def test_fd_jv_close_to_exact(S, name):
     """Finite-difference JFNK product vs the exact derivative: O(eps) truncation, eps ~ 1e-8 relative."""
     prob = Problem(**CASES[name])

@@ -165,3 +165,22 @@ def test_mixed_precision_density_wave_3d(S):
         ctx.advance_slab()
         U = prob.from_ext(ctx.get_slab())
     assert rel_lgl(prob, U, U_or) <= 1e-11, rel_lgl(prob, U, U_or)
+
+
+@pytest.mark.parametrize("eq,dim,cells,N,s,nu", [("advection", 2, (6, 5), 3, 3, 0.01),
+                                                ("advection", 1, (8,), 4, 4, 0.05),
+                                                ("burgers", 2, (5, 5), 3, 3, 0.02)])
+def test_viscous_slab_matches_oracle(S, eq, dim, cells, N, s, nu):
+    """Slab solves with the interior-penalty viscous term (FP64 FD Jv; mixed precision with
+    exact FP32 Jv) against the oracle's."""
+    prob = Problem(dim=dim, cells=cells, N=N, s=s, eq=eq, dt=0.02, nu=nu, adv=(0.7, -0.4))
+    X = prob.grid.coordinates()
+    u0 = inputs.burgers_fourier(X[0], X[1], 1003) if dim == 2 else inputs.sine(X[0])
+    U_or = ost.solve_slab_newton_gmres("stdg", prob.F, u0, prob.dt, prob.s, rtol=1e-14, atol=1e-13,
+                                       gmres_tol=1e-11, gmres_m=40)
+    for extra in (dict(), dict(precision=S.MIXED_FP32, jv_mode=S.JV_EXACT, gmres_rtol=1e-4, newton_maxit=30)):
+        with S.Context(prob.config(**dict(TIGHT, **extra))) as ctx:
+            ctx.set_state(np.ascontiguousarray(u0).ravel())
+            ctx.advance_slab()
+            U = prob.from_ext(ctx.get_slab())
+        assert rel_lgl(prob, U, U_or) <= 1e-11, (extra, rel_lgl(prob, U, U_or))
