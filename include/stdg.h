@@ -284,7 +284,41 @@ stdg_status stdg_batch_remove(stdg_batch* b, int slot);
 /* Device bytes a problem would take in the arena (0 if invalid). */
 size_t stdg_batch_slot_bytes(const stdg_batch* b, const stdg_config_desc* inst);
 size_t stdg_batch_free_bytes(const stdg_batch* b);
+/* Slots that finished (as of the last step/run) and are not removed yet:
+ * writes up to cap ids to slots, returns how many there are.  Host-side, no
+ * synchronisation. */
+int stdg_batch_done_slots(const stdg_batch* b, int* slots, int cap);
 const char* stdg_batch_last_error(const stdg_batch* b);
+
+/* ==================================================================== server
+ * Continuous batching of slab solves (no counterpart in the paper).  A worker
+ * thread owns a batch (above) on the device that is current at creation and
+ * its own CUDA stream.  Submitted requests queue in arrival order; between
+ * groups of ticks_per_round ticks the worker admits queued requests while the
+ * arena (hbm_budget_bytes) and the slot table have room, so requests that
+ * arrive while others run join their launches as memory frees up, and it
+ * retires finished slots (result copied back, memory released).  A request
+ * that alone exceeds the arena finishes with STDG_ERR_OOM.  A result is the
+ * same as the batch would give for the request alone (see the batch section).
+ * Submit and poll may be called from any host thread. */
+typedef struct stdg_server stdg_server;
+stdg_status stdg_server_create(const stdg_batch_desc* desc, int ticks_per_round, stdg_server** out);
+/* Stops the worker (requests still queued or running are dropped). */
+stdg_status stdg_server_destroy(stdg_server* s);
+/* Queue one slab solve: inst as for stdg_batch_add, u0 = host initial state
+ * (copied).  *ticket identifies the request. */
+stdg_status stdg_server_submit(stdg_server* s, const stdg_config_desc* inst, const double* u0,
+                               unsigned long long* ticket);
+/* Wait up to wait_s seconds (0: do not wait) for the request.  *done = 1 once
+ * it finished; then *status, *stats, the new state u (host, state length of
+ * the request; may be NULL) and times[3] = {queue wait (submit -> admission),
+ * service (admission -> done), latency (submit -> done)} in seconds (may be
+ * NULL) are filled and the ticket is released. */
+stdg_status stdg_server_poll(stdg_server* s, unsigned long long ticket, double wait_s, int* done, int* status,
+                             stdg_slab_stats* stats, double* u, double* times);
+/* Counters since creation; returns the worker's fatal status (STDG_OK if none). */
+stdg_status stdg_server_counters(stdg_server* s, unsigned long long* admitted, unsigned long long* completed,
+                                 unsigned long long* ticks, int* queued, int* running, int* max_running);
 
 const char* stdg_last_error(const stdg_ctx* ctx);
 const char* stdg_status_string(stdg_status st);

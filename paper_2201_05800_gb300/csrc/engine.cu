@@ -566,6 +566,17 @@ stdg_status stdg_batch_remove(stdg_batch* b, int slot) {
   return STDG_OK;
 }
 
+int stdg_batch_done_slots(const stdg_batch* b, int* slots, int cap) {
+  if (!b) return 0;
+  int n = 0;
+  for (int i = 0; i < (int)b->slots.size(); ++i)
+    if (b->slots[i].used && b->slots[i].done) {
+      if (slots && n < cap) slots[n] = i;
+      ++n;
+    }
+  return n;
+}
+
 const char* stdg_batch_last_error(const stdg_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
 }  // extern "C"

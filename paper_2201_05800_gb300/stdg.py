@@ -296,6 +296,18 @@ _BATCH_SIGS = {
     "stdg_batch_free_bytes": (ctypes.c_size_t, [_P]),
     "stdg_batch_last_error": (ctypes.c_char_p, [_P]),
 }
+_BATCH_SIGS.update({
+    "stdg_batch_done_slots": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    "stdg_server_create": (ctypes.c_int, [ctypes.POINTER(stdg_batch_desc), ctypes.c_int, ctypes.POINTER(_P)]),
+    "stdg_server_destroy": (ctypes.c_int, [_P]),
+    "stdg_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(stdg_config_desc), _P,
+                                          ctypes.POINTER(ctypes.c_ulonglong)]),
+    "stdg_server_poll": (ctypes.c_int, [_P, ctypes.c_ulonglong, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(stdg_slab_stats), _P,
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "stdg_server_counters": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_ulonglong)] * 3
+                             + [ctypes.POINTER(ctypes.c_int)] * 3),
+})
 _SIGS.update(_BATCH_SIGS)
 
 
@@ -398,6 +410,81 @@ class Batch:
     def remove(self, slot):
         self._check(self._lib.stdg_batch_remove(self._h, slot))
         self._descs.pop(slot, None)
+
+
+def _desc_state_len(d):
+    n = d.dim + 2 if d.equation == EULER else 1
+    for a in range(d.dim):
+        n *= d.cells[a] * (d.N + 1)
+    return n
+
+
+class Server:
+    """Owns one stdg_server (continuous batching of slab solves on a worker thread)."""
+
+    def __init__(self, dim, equation, max_slots, hbm_budget_bytes, ticks_per_round=4):
+        lib = load()
+        self._lib = lib
+        self.desc = stdg_batch_desc(dim, equation, max_slots, hbm_budget_bytes)
+        h = _P()
+        st = lib.stdg_server_create(ctypes.byref(self.desc), ticks_per_round, ctypes.byref(h))
+        if st != 0:
+            raise StdgError(st, "stdg_server_create failed")
+        self._h = h
+        self._lens = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.stdg_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, desc, u0):
+        """Queue one request (u0: host FP64 state); returns its ticket."""
+        u0 = np.ascontiguousarray(u0, dtype=np.float64).ravel()
+        if u0.size != _desc_state_len(desc):
+            raise ValueError("u0 has %d values, the problem needs %d" % (u0.size, _desc_state_len(desc)))
+        t = ctypes.c_ulonglong(0)
+        st = self._lib.stdg_server_submit(self._h, ctypes.byref(desc), ctypes.c_void_p(u0.ctypes.data), ctypes.byref(t))
+        if st != 0:
+            raise StdgError(st, "stdg_server_submit failed")
+        self._lens[t.value] = u0.size
+        return t.value
+
+    def poll(self, ticket, wait_s=0.0):
+        """None while the request runs; else dict(status, stats, u, queue_s, service_s, latency_s)."""
+        done, status = ctypes.c_int(0), ctypes.c_int(0)
+        stats = stdg_slab_stats()
+        u = np.empty(self._lens[ticket])
+        times = (ctypes.c_double * 3)()
+        st = self._lib.stdg_server_poll(self._h, ticket, float(wait_s), ctypes.byref(done), ctypes.byref(status),
+                                        ctypes.byref(stats), ctypes.c_void_p(u.ctypes.data), times)
+        if st != 0:
+            raise StdgError(st, "stdg_server_poll failed")
+        if not done.value:
+            return None
+        self._lens.pop(ticket, None)
+        return {"status": status.value, "stats": stats.as_dict(), "u": u, "queue_s": times[0],
+                "service_s": times[1], "latency_s": times[2]}
+
+    def counters(self):
+        a, c, t = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0), ctypes.c_ulonglong(0)
+        q, r, mr = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        st = self._lib.stdg_server_counters(self._h, ctypes.byref(a), ctypes.byref(c), ctypes.byref(t),
+                                            ctypes.byref(q), ctypes.byref(r), ctypes.byref(mr))
+        return {"admitted": a.value, "completed": c.value, "ticks": t.value, "queued": q.value,
+                "running": r.value, "max_running": mr.value, "fatal": st}
 
 
 def version():

@@ -87,3 +87,20 @@ def test_batch_validation_without_gpu(lib):
         assert not h.value
     assert lib.stdg_batch_destroy(None) == 1
     assert lib.stdg_batch_free_bytes(None) == 0
+
+
+def test_server_without_gpu(lib):
+    """Server creation validates its arguments first, then reports the missing device as a
+    status (no worker thread is left behind)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2201_05800_gb300 import stdg
+    h = ctypes.c_void_p()
+    bad = stdg.stdg_batch_desc(2, stdg.EULER, 0, 1 << 20)
+    assert lib.stdg_server_create(ctypes.byref(bad), 4, ctypes.byref(h)) == 1
+    ok = stdg.stdg_batch_desc(2, stdg.EULER, 4, 1 << 20)
+    assert lib.stdg_server_create(ctypes.byref(ok), 0, ctypes.byref(h)) == 1
+    assert lib.stdg_server_create(ctypes.byref(ok), 4, ctypes.byref(h)) == 3
+    assert not h.value
+    assert lib.stdg_server_destroy(None) == 1
