@@ -352,7 +352,11 @@ def gpu_arm(args):
 
         # ---- the same slabs on the mixed-precision path (FP32 exact Jv and Krylov basis,
         #      FP64 Newton residual and update): throughput and distance to the FP64 path
-        mixed = _mixed_path(stdg, desc, u0, args, stream, u_fp64, ws)
+        mixed = _mixed_path(stdg, desc, u0, args, stream, u_fp64, ws) if "mixed" in args.legs else None
+        batched = _batched_leg(stdg, stream, args.batch_instances, args.batch_sequential) \
+            if "batched" in args.legs and ws == 1 else None
+        served = _serving_leg(stdg, [int(r) for r in args.serve_rates.split(",")], args.serve_requests) \
+            if "serving" in args.legs and ws == 1 else None
 
     lat_ms = sorted(1e3 * x for x in lat)
     cpu = None
@@ -387,7 +391,8 @@ def gpu_arm(args):
                 "roofline": roofline, "clocks": clocks,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hin.numel() * 8),
                         "d2h_bytes_per_step": int(hout.numel() * 8)},
-                "gpu_launches": launches, "cpu_baseline": cpu, "mixed_fp32": mixed}
+                "gpu_launches": launches, "cpu_baseline": cpu, "mixed_fp32": mixed,
+                "batched": batched, "served": served}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -435,6 +440,202 @@ def _mixed_path(stdg, desc, u0, args, stream, u_ref, ws):
             "kernel_launches": {k: v["launches"] for k, v in prof.items()}}
 
 
+# ----------------------------------------------------------------------------- batched / served legs
+
+WORK_TOL = dict(newton_rtol=1e-10, newton_atol=0.0, newton_maxit=30, gmres_m=30, gmres_rtol=1e-3)
+
+
+class _Coords:
+    """Node coordinates per (equation, box, side, N), taken from the library (a small context)."""
+
+    def __init__(self, stdg):
+        self.stdg, self.cache = stdg, {}
+
+    def __call__(self, eq, box, side, N):
+        key = (eq, box, side, N)
+        if key not in self.cache:
+            S = self.stdg
+            d = S.make_config(dim=2, cells=[side, side, 1], lo=[0, 0, 0], hi=[box, box, 1], N=N, s=2, equation=eq,
+                              dt=1.0, gmres_m=1)
+            with S.Context(d) as c:
+                self.cache[key] = c.node_coordinates()
+        return self.cache[key]
+
+
+def _burgers_instances(stdg, n):
+    """The batched viscous Burgers workload: instance i from seed 1000 + i (grid side in
+    {8,16,32,64}, N in 2..6, s in 2..5, viscosity log-uniform in [1e-3, 1e-1]), 8 Fourier modes
+    of amplitude 0.5 on the periodic unit square, dt = 0.5 h / max|u0| (CFL 0.5)."""
+    import numpy as np
+    from paper_2201_05800_gb300 import inputs
+    xy = _Coords(stdg)
+    out = []
+    for i in range(n):
+        sp = inputs.burgers_instance(i)
+        X = xy(stdg.BURGERS, 1.0, sp["side"], sp["N"])
+        u0 = np.ascontiguousarray(inputs.burgers_fourier(X[:, 0], X[:, 1], sp["seed"]).ravel())
+        dt = 0.5 * (1.0 / sp["side"]) / float(np.max(np.abs(u0)))
+        d = stdg.make_config(dim=2, cells=[sp["side"], sp["side"], 1], lo=[0, 0, 0], hi=[1, 1, 1], N=sp["N"],
+                             s=sp["s"], equation=stdg.BURGERS, dt=dt, viscosity=sp["nu"], **WORK_TOL)
+        out.append((d, u0, u0.size * sp["s"]))
+    return out
+
+
+def _vortex_requests(stdg, n, seed=7):
+    """Served requests: single-slab solves of the 2D Euler vortex on [0,10]^2, grid side uniform
+    in {16,32,64,128}, N uniform in 2..7, s uniform in 2..5, CFL 0.5 (seeded)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    xy = _Coords(stdg)
+    out = []
+    for _ in range(n):
+        side = int(rng.choice([16, 32, 64, 128]))
+        N = int(rng.integers(2, 8))
+        s = int(rng.integers(2, 6))
+        X = xy(stdg.EULER, 10.0, side, N)
+        u0 = np.ascontiguousarray(_vortex_state(X).ravel())
+        dt = _cfl_dt(u0.reshape(-1, 4), 10.0 / side)
+        d = stdg.make_config(dim=2, cells=[side, side, 1], lo=[0, 0, 0], hi=[10, 10, 1], N=N, s=s,
+                             equation=stdg.EULER, gamma=WORKLOAD["gamma"], dt=dt, **WORK_TOL)
+        out.append((d, u0, u0.size * s))
+    return out
+
+
+def _sequential_config(stdg, d):
+    """The plain one-solve-at-a-time GPU path at the same accuracy: a context with FP32 exact
+    Jacobian-vector products, FP64 Newton and the point-block preconditioner (restarted GMRES)."""
+    import ctypes
+    dm = stdg.stdg_config_desc()
+    ctypes.memmove(ctypes.byref(dm), ctypes.byref(d), ctypes.sizeof(d))
+    dm.precision, dm.jv_mode, dm.precond, dm.gmres_maxit = stdg.MIXED_FP32, stdg.JV_EXACT, stdg.PRECOND_POINT_BLOCK, 600
+    return dm
+
+
+def _run_batch(stdg, B, items):
+    """Admit items in arrival order while the arena has room, tick, retire: returns per-item
+    (status, stats, state)."""
+    pending = list(range(len(items)))
+    slots, res = {}, {}
+    while pending or slots:
+        while pending:
+            sl = B.try_add(items[pending[0]][0], items[pending[0]][1])
+            if sl is None:
+                break
+            slots[sl] = pending.pop(0)
+        if not slots:
+            raise RuntimeError("an item does not fit the arena")
+        B.step(8)
+        for sl in B.done_slots():
+            _, st, stats = B.query(sl)
+            res[slots.pop(sl)] = (st, stats, B.get_state(sl))
+            B.remove(sl)
+    return [res[i] for i in range(len(items))]
+
+
+def _batched_leg(stdg, stream, n_inst, n_seq):
+    import numpy as np
+    import torch
+    items = _burgers_instances(stdg, n_inst)
+    free, _ = torch.cuda.mem_get_info()
+    arena = int(free * 0.7)
+    with stdg.Batch(2, stdg.BURGERS, n_inst, arena, stream.cuda_stream) as B:
+        need = sum(B.slot_bytes(d) for d, _, _ in items)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = _run_batch(stdg, B, items)
+        torch.cuda.synchronize()
+        T = time.perf_counter() - t0
+        # the same first n_seq instances alone in the batch engine, for the like-for-like comparison
+        t1 = time.perf_counter()
+        out_small = _run_batch(stdg, B, items[:n_seq])
+        torch.cuda.synchronize()
+        T_small = time.perf_counter() - t1
+    evals = sum((st["residual_evals"] + st["jv_evals"]) * dof for (_, st, _), (_, _, dof) in zip(out, items))
+    statuses = [st for st, _, _ in out]
+    # sequential plain path on the first n_seq instances
+    seq = []
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    for d, u0, _ in items[:n_seq]:
+        with stdg.Context(_sequential_config(stdg, d), stream.cuda_stream) as c:
+            c.set_state(u0)
+            st = c.advance_slab(check=False)
+            seq.append((st["status"], c.get_state()))
+    torch.cuda.synchronize()
+    T_seq = time.perf_counter() - t2
+    diffs = [float(np.linalg.norm(a[2] - b[1]) / np.linalg.norm(b[1])) for a, b in zip(out[:n_seq], seq)
+             if a[0] == 0 and b[0] == 0]
+    its = [st["gmres_its"] for _, st, _ in out]
+    return {"workload": "%d independent 2D viscous Burgers instances (seed 1000+i; side in {8,16,32,64}, N 2-6, "
+                        "s 2-5, nu log-uniform [1e-3,1e-1]), one slab each, FP32 Krylov + FP64 Newton "
+                        "refinement, Newton rtol 1e-10, FGMRES(30) rtol 1e-3" % n_inst,
+            "instances": n_inst, "dof_total": int(sum(x[2] for x in items)), "arena_gb": arena / 1e9,
+            "slot_memory_gb": need / 1e9, "seconds": T, "instances_per_s": n_inst / T,
+            "gdof_evals_per_s": evals / T / 1e9,
+            "status_counts": {str(k): statuses.count(k) for k in sorted(set(statuses))},
+            "gmres_its_mean": float(np.mean(its)), "gmres_its_max": int(max(its)),
+            "vs_sequential": {"instances": n_seq, "batched_s": T_small, "sequential_s": T_seq,
+                              "batched_instances_per_s": n_seq / T_small, "sequential_instances_per_s": n_seq / T_seq,
+                              "speedup": T_seq / T_small,
+                              "max_rel_diff_to_sequential": max(diffs) if diffs else None,
+                              "sequential_path": "stdg_advance_slab per instance (context per instance), FP32 exact "
+                                                 "Jv + point-block preconditioner, restarted GMRES(30)"}}
+
+
+def _serving_leg(stdg, rates, n_req):
+    import numpy as np
+    import torch
+    reqs = _vortex_requests(stdg, n_req)
+    free, _ = torch.cuda.mem_get_info()
+    arena = int(free * 0.5)
+    rng = np.random.default_rng(7)
+    out = {"workload": "single-slab 2D Euler vortex solves on [0,10]^2, side in {16,32,64,128}, N 2-7, s 2-5, "
+                       "CFL 0.5, Newton rtol 1e-10, FGMRES(30) rtol 1e-3; Poisson arrivals (seed 7)",
+           "requests_per_rate": n_req, "arena_gb": arena / 1e9, "rates": {}}
+    # service times of the plain sequential GPU path (solve only, contexts created outside the timing)
+    svc, seq_status = [], []
+    stream = torch.cuda.Stream()
+    for d, u0, _ in reqs:
+        with stdg.Context(_sequential_config(stdg, d), stream.cuda_stream) as c:
+            c.set_state(u0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = c.advance_slab(check=False)
+            svc.append(time.perf_counter() - t0)
+            seq_status.append(st["status"])
+    for rate in rates:
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+        with stdg.Server(2, stdg.EULER, max(64, n_req), arena) as srv:
+            t0 = time.perf_counter()
+            tickets = []
+            for (d, u0, _), ta in zip(reqs, arrivals):
+                while time.perf_counter() - t0 < ta:
+                    pass
+                tickets.append(srv.submit(d, u0))
+            res = [srv.poll(t, wait_s=600.0) for t in tickets]
+            T = time.perf_counter() - t0
+            cnt = srv.counters()
+        lat = sorted(r["latency_s"] for r in res)
+        # the sequential path under the same arrivals (one queue, measured service times)
+        fin, seq_lat = 0.0, []
+        for ta, sv in zip(arrivals, svc):
+            fin = max(fin, ta) + sv
+            seq_lat.append(fin - ta)
+        seq_lat.sort()
+        pct = lambda v, q: 1e3 * v[min(len(v) - 1, int(q * len(v)))]
+        out["rates"][str(rate)] = {
+            "served": {"p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "solves_per_s": n_req / T,
+                       "max_running": cnt["max_running"],
+                       "statuses": {str(k): [r["status"] for r in res].count(k)
+                                    for k in sorted({r["status"] for r in res})}},
+            "sequential": {"p50_ms": pct(seq_lat, 0.5), "p99_ms": pct(seq_lat, 0.99),
+                           "solves_per_s": n_req / fin}}
+    out["sequential_path"] = ("stdg_advance_slab per request in arrival order (FP32 exact Jv, point-block "
+                              "preconditioner); latencies from the measured service times under the same arrivals")
+    out["sequential_statuses"] = {str(k): seq_status.count(k) for k in sorted(set(seq_status))}
+    return out
+
+
 def _ncu_traffic():
     """DRAM bytes per launch of the FD Jv kernel from the committed ncu summary, or None."""
     p = os.path.join(ROOT, "profiles", "jv_fd_euler2d_vortex64.txt")
@@ -456,6 +657,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="mixed,batched,serving",
+                    help="extra legs after the main FP64 line: mixed,batched,serving")
+    ap.add_argument("--batch-instances", type=int, default=4096)
+    ap.add_argument("--batch-sequential", type=int, default=48,
+                    help="instances solved one at a time for the batched-vs-sequential comparison")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rates", default="100,1000,5000")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

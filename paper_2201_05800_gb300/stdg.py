@@ -411,6 +411,13 @@ class Batch:
         self._check(self._lib.stdg_batch_remove(self._h, slot))
         self._descs.pop(slot, None)
 
+    def done_slots(self):
+        """Slots that finished as of the last step/run and are not removed yet."""
+        n = self._lib.stdg_batch_done_slots(self._h, None, 0)
+        buf = (ctypes.c_int * max(n, 1))()
+        n = self._lib.stdg_batch_done_slots(self._h, buf, n)
+        return list(buf[:n])
+
 
 def _desc_state_len(d):
     n = d.dim + 2 if d.equation == EULER else 1
