@@ -582,6 +582,10 @@ def _batched_leg(stdg, stream, n_inst, n_seq):
                                                  "Jv + point-block preconditioner, restarted GMRES(30)"}}
 
 
+SERVE_SHARE_QUANTUM = 262144.0  # DOF: a request of L DOF advances every round(L / quantum)-th tick (<= 16)
+SERVE_SHARE_MAX_STRIDE = 16
+
+
 def _serving_leg(stdg, rates, n_req):
     import numpy as np
     import torch
@@ -606,6 +610,7 @@ def _serving_leg(stdg, rates, n_req):
     for rate in rates:
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
         with stdg.Server(2, stdg.EULER, max(64, n_req), arena) as srv:
+            srv.configure(share_quantum=SERVE_SHARE_QUANTUM, share_max_stride=SERVE_SHARE_MAX_STRIDE)
             t0 = time.perf_counter()
             tickets = []
             for (d, u0, _), ta in zip(reqs, arrivals):
@@ -630,6 +635,8 @@ def _serving_leg(stdg, rates, n_req):
                                     for k in sorted({r["status"] for r in res})}},
             "sequential": {"p50_ms": pct(seq_lat, 0.5), "p99_ms": pct(seq_lat, 0.99),
                            "solves_per_s": n_req / fin}}
+    out["scheduling"] = {"share_quantum_dof": SERVE_SHARE_QUANTUM, "share_max_stride": SERVE_SHARE_MAX_STRIDE,
+                         "graphs": True, "autotune": True}
     out["sequential_path"] = ("stdg_advance_slab per request in arrival order (FP32 exact Jv, point-block "
                               "preconditioner); latencies from the measured service times under the same arrivals")
     out["sequential_statuses"] = {str(k): seq_status.count(k) for k in sorted(set(seq_status))}

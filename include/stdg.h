@@ -284,6 +284,18 @@ stdg_status stdg_batch_remove(stdg_batch* b, int slot);
 /* Device bytes a problem would take in the arena (0 if invalid). */
 size_t stdg_batch_slot_bytes(const stdg_batch* b, const stdg_config_desc* inst);
 size_t stdg_batch_free_bytes(const stdg_batch* b);
+/* Scheduling knobs of a batch (defaults: 0, 16, 1, 1).
+ * share_quantum > 0 enables size-aware sharing: a slot of L space-time DOF
+ *   takes part only in every k-th tick, k = clamp(round(L / share_quantum), 1,
+ *   share_max_stride), so that very large slots do not set the tick time of
+ *   the small ones (a slot's result does not change; only when it advances).
+ * use_graphs: each stdg_batch_step is replayed as one captured CUDA graph of
+ *   its ticks (recaptured when the slot set or the tick count changes).
+ * autotune: elements per CTA of the operator kernels chosen by timing the
+ *   candidates on the first slot of each (dim, equation, N, s) class, cached
+ *   for the process (every later slot of the class gets the same tiles). */
+stdg_status stdg_batch_configure(stdg_batch* b, double share_quantum, int share_max_stride, int use_graphs,
+                                 int autotune);
 /* Slots that finished (as of the last step/run) and are not removed yet:
  * writes up to cap ids to slots, returns how many there are.  Host-side, no
  * synchronisation. */
@@ -316,6 +328,9 @@ stdg_status stdg_server_submit(stdg_server* s, const stdg_config_desc* inst, con
  * NULL) are filled and the ticket is released. */
 stdg_status stdg_server_poll(stdg_server* s, unsigned long long ticket, double wait_s, int* done, int* status,
                              stdg_slab_stats* stats, double* u, double* times);
+/* The batch knobs of stdg_batch_configure, applied before the worker's next round. */
+stdg_status stdg_server_configure(stdg_server* s, double share_quantum, int share_max_stride, int use_graphs,
+                                  int autotune);
 /* Counters since creation; returns the worker's fatal status (STDG_OK if none). */
 stdg_status stdg_server_counters(stdg_server* s, unsigned long long* admitted, unsigned long long* completed,
                                  unsigned long long* ticks, int* queued, int* running, int* max_running);

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -112,6 +113,14 @@ struct stdg_batch {
   bool dirty = true;
   size_t smem64 = 0, smem32 = 0;
   std::string err;
+  int* tick_d = nullptr;        // device tick counter
+  double share_quantum = 0.0;   // size-aware sharing (0: every slot in every tick)
+  int share_max_stride = 16;
+  bool use_graphs = true;       // capture the ticks of a step as one CUDA graph
+  cudaGraphExec_t gexec = nullptr;
+  int gticks = 0;
+  bool autotune = true;         // pick elements per CTA of the op kernels by measurement
+  bool own_stream = false;      // created here when the caller passed the legacy default stream
 };
 
 namespace {
@@ -140,6 +149,17 @@ struct BDev {
 };
 
 int ncomp(int eq, int dim) { return eq == STDG_EULER ? dim + 2 : 1; }
+
+// Measured elements-per-CTA of the two op kernels per problem class (dim, equation, n, s),
+// shared by all batches of the process so that a class always gets the same tiles.
+struct TuneKey {
+  int dim, eq, n, s;
+  bool operator<(const TuneKey& o) const {
+    return dim != o.dim ? dim < o.dim : eq != o.eq ? eq < o.eq : n != o.n ? n < o.n : s < o.s;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;
 
 bool physics_supported(int dim, int eq) {
   return (eq == STDG_ADVECTION && (dim == 1 || dim == 2)) || (eq == STDG_BURGERS && dim == 2) ||
@@ -225,6 +245,18 @@ cudaError_t grow(T** p, size_t* cap, size_t need, cudaStream_t st) {
   return cudaSuccess;
 }
 
+cudaError_t physics(stdg_batch* b, const EngLaunch& L, int prepare) {
+  if (b->d.equation == STDG_EULER && b->d.dim == 2) return eng_physics_euler2(L, b->st, prepare);
+  if (b->d.equation == STDG_BURGERS && b->d.dim == 2) return eng_physics_burgers2(L, b->st, prepare);
+  return eng_physics_advection(b->d.dim, L, b->st, prepare);
+}
+
+cudaError_t probe(const stdg_batch* b, int mode, const OpArgs<double>& a64, const OpArgs<float>& a32) {
+  if (b->d.equation == STDG_EULER && b->d.dim == 2) return eng_probe_euler2(mode, a64, a32, b->st);
+  if (b->d.equation == STDG_BURGERS && b->d.dim == 2) return eng_probe_burgers2(mode, a64, a32, b->st);
+  return eng_probe_advection(b->d.dim, mode, a64, a32, b->st);
+}
+
 // Work-item lists and slot records of the active slots.
 stdg_status rebuild(stdg_batch* b) {
   std::vector<EngItem> op, ch;
@@ -241,6 +273,22 @@ stdg_status rebuild(stdg_batch* b) {
     b->smem64 = std::max(b->smem64, operator_smem_bytes(l.dim, l.r, 8, kModeResidual, l.n, l.s, hs.epb64));
     b->smem32 = std::max(b->smem32, operator_smem_bytes(l.dim, l.r, 4, kModeJvExact, l.n, l.s, hs.epb32));
     BCK(b, cudaMemcpyAsync(b->buf + id, &hs.buf, sizeof(SlotBuf), cudaMemcpyHostToDevice, b->st));
+  }
+  // size-aware sharing: stride = clamp(round(L / quantum), 1, max_stride); offsets spread the
+  // large slots over the ticks of a period
+  int next_off = 0;
+  for (int id : b->active) {
+    HostSlot& hs = b->slots[id];
+    int stride = 1;
+    if (b->share_quantum > 0.0)
+      stride = (int)std::min<double>(b->share_max_stride, std::max(1.0, std::floor(hs.lay.L / b->share_quantum + 0.5)));
+    hs.buf.stride = stride;
+    hs.buf.offset = stride > 1 ? (next_off++ % stride) : 0;
+    BCK(b, cudaMemcpyAsync(b->buf + id, &hs.buf, sizeof(SlotBuf), cudaMemcpyHostToDevice, b->st));
+  }
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
   }
   BCK(b, grow(&b->op_items, &b->cap_op, std::max<size_t>(op.size(), 1), b->st));
   size_t capc = b->cap_chunk;
@@ -260,6 +308,13 @@ stdg_status rebuild(stdg_batch* b) {
   if (!b->active.empty())
     BCK(b, cudaMemcpyAsync(b->active_d, b->active.data(), b->active.size() * sizeof(int), cudaMemcpyHostToDevice,
                            b->st));
+  {
+    EngLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.op_smem64 = b->smem64;
+    L.op_smem32 = b->smem32;
+    BCK(b, physics(b, L, 1));
+  }
   // the host vectors are pageable: make the copies complete before they go out of scope
   BCK(b, cudaStreamSynchronize(b->st));
   b->n_op = cnt[0];
@@ -268,11 +323,8 @@ stdg_status rebuild(stdg_batch* b) {
   return STDG_OK;
 }
 
+// Launches of one tick (the lists must be current).
 stdg_status tick(stdg_batch* b) {
-  if (b->dirty) {
-    stdg_status s = rebuild(b);
-    if (s != STDG_OK) return s;
-  }
   if (b->active.empty()) return STDG_OK;
   EngLaunch L;
   L.op_items = b->op_items;
@@ -292,12 +344,10 @@ stdg_status tick(stdg_batch* b) {
   L.buf = b->buf;
   L.ctl = b->ctl;
   L.partials = b->partials;
-  cudaError_t e;
-  if (b->d.equation == STDG_EULER && b->d.dim == 2) e = eng_physics_euler2(L, b->st);
-  else if (b->d.equation == STDG_BURGERS && b->d.dim == 2) e = eng_physics_burgers2(L, b->st);
-  else e = eng_physics_advection(b->d.dim, L, b->st);
+  L.tick = b->tick_d;
+  cudaError_t e = physics(b, L, 0);
   if (e != cudaSuccess) return bfail(b, STDG_ERR_CUDA, std::string("engine physics launch: ") + cudaGetErrorString(e));
-  e = eng_generic_launch(L, b->st);
+  e = eng_tick_tail(L, b->st);
   if (e != cudaSuccess) return bfail(b, STDG_ERR_CUDA, std::string("engine launch: ") + cudaGetErrorString(e));
   return STDG_OK;
 }
@@ -332,6 +382,67 @@ stdg_status refresh(stdg_batch* b, int* working) {
   return STDG_OK;
 }
 
+// Elements per CTA of the two op kernels for the slot's class: cached, else measured on the
+// new slot's own data (U = 1 (x) u^n; outputs into R and the unused basis row V_1).
+stdg_status tune(stdg_batch* b, const Layout& l, int eq, const OpArgs<double>& k64, const OpArgs<float>& k32,
+                 const SlotBuf& sb, int* epb64, int* epb32) {
+  const TuneKey key{l.dim, eq, l.n, l.s};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      *epb64 = it->second.first;
+      *epb32 = it->second.second;
+      return STDG_OK;
+    }
+  }
+  const int r = ncomp(eq, l.dim);
+  const int maxe = (int)std::min<long long>(std::max(1, 256 / l.nd), l.nelem);
+  const int cand[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 24, 28, 32};
+  cudaEvent_t e0, e1;
+  BCK(b, cudaEventCreate(&e0));
+  BCK(b, cudaEventCreate(&e1));
+  int best[2] = {*epb64, *epb32};
+  for (int mode = 0; mode < 2; ++mode) {
+    float best_ms = 1e30f;
+    for (int c : cand) {
+      if (c > maxe) break;
+      if (operator_smem_bytes(l.dim, r, mode == 0 ? 8 : 4, mode == 0 ? kModeResidual : kModeJvExact, l.n, l.s, c) >
+          kOpSmemCap)
+        break;
+      OpArgs<double> a = k64;
+      OpArgs<float> f = k32;
+      a.epb = c;
+      a.out = sb.R;
+      f.epb = c;
+      f.U = sb.U32;
+      f.v = sb.U32;
+      f.out = sb.V + l.L;
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        BCK(b, cudaEventRecord(e0, b->st));
+        BCK(b, probe(b, mode, a, f));
+        BCK(b, cudaEventRecord(e1, b->st));
+        BCK(b, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BCK(b, cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) ms_min = std::min(ms_min, ms);  // first launch warms up
+      }
+      if (ms_min < best_ms * 0.97f) {  // prefer the smaller tile unless clearly faster
+        best_ms = ms_min;
+        best[mode] = c;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto ins = g_tune.emplace(key, std::make_pair(best[0], best[1]));
+  *epb64 = ins.first->second.first;
+  *epb32 = ins.first->second.second;
+  return STDG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -349,6 +460,16 @@ stdg_status stdg_batch_create(const stdg_batch_desc* desc, void* cuda_stream, st
     delete b;
     return STDG_ERR_CUDA;
   }
+  if (!b->st) {
+    // graph capture needs a stream of its own; every batch call returns after its work
+    // completed, so the caller sees the same ordering as on the default stream
+    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete b;
+      return STDG_ERR_CUDA;
+    }
+    b->own_stream = true;
+  }
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
   if (b->sms < 1) b->sms = 1;
   const int ns = desc->max_slots;
@@ -362,6 +483,7 @@ stdg_status stdg_batch_create(const stdg_batch_desc* desc, void* cuda_stream, st
   ok = ok && cudaMalloc(&b->active_d, ns * sizeof(int)) == cudaSuccess;
   ok = ok && cudaMalloc(&b->phase_d, ns * sizeof(int)) == cudaSuccess;
   ok = ok && cudaMallocHost(&b->phase_h, ns * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->tick_d, sizeof(int)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     stdg_batch_destroy(b);
@@ -369,6 +491,7 @@ stdg_status stdg_batch_create(const stdg_batch_desc* desc, void* cuda_stream, st
   }
   if (cudaMemsetAsync(b->ctl, 0, ns * sizeof(SlotCtl), b->st) != cudaSuccess ||
       cudaMemsetAsync(b->counts, 0, 2 * sizeof(int), b->st) != cudaSuccess ||
+      cudaMemsetAsync(b->tick_d, 0, sizeof(int), b->st) != cudaSuccess ||
       cudaStreamSynchronize(b->st) != cudaSuccess) {
     cudaGetLastError();
     stdg_batch_destroy(b);
@@ -383,11 +506,13 @@ stdg_status stdg_batch_destroy(stdg_batch* b) {
   if (!b) return STDG_ERR_INVALID_ARG;
   BDev g(b->device);
   cudaStreamSynchronize(b->st);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
   void* ps[] = {b->arena_base, b->ctl, b->a64, b->a32, b->buf, b->counts, b->active_d, b->phase_d,
-                b->op_items, b->chunk_items, b->partials};
+                b->op_items, b->chunk_items, b->partials, b->tick_d};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (b->phase_h) cudaFreeHost(b->phase_h);
+  if (b->own_stream) cudaStreamDestroy(b->st);
   cudaGetLastError();
   delete b;
   return STDG_OK;
@@ -477,6 +602,14 @@ stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* d, const doubl
   BCK(b, cudaMemcpyAsync(sb.uprev, u0, l.S * sizeof(double),
                          kind == STDG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, b->st));
   BCK(b, eng_init_slot(sb, b->st));
+  if (b->autotune) {
+    stdg_status ts = tune(b, l, d->equation, k64, k32, sb, &hs.epb64, &hs.epb32);
+    if (ts != STDG_OK) return ts;
+    k64.epb = hs.epb64;
+    k32.epb = hs.epb32;
+    BCK(b, cudaMemcpyAsync(b->a64 + id, &k64, sizeof(k64), cudaMemcpyHostToDevice, b->st));
+    BCK(b, cudaMemcpyAsync(b->a32 + id, &k32, sizeof(k32), cudaMemcpyHostToDevice, b->st));
+  }
   // the staging structs live on this stack frame
   BCK(b, cudaStreamSynchronize(b->st));
   b->active.push_back(id);
@@ -488,11 +621,50 @@ stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* d, const doubl
 stdg_status stdg_batch_step(stdg_batch* b, int ticks, int* working) {
   if (!b || ticks < 1) return STDG_ERR_INVALID_ARG;
   BDev g(b->device);
-  for (int t = 0; t < ticks; ++t) {
-    stdg_status s = tick(b);
+  if (b->dirty) {
+    stdg_status s = rebuild(b);
     if (s != STDG_OK) return s;
   }
+  if (!b->active.empty()) {
+    if (b->use_graphs) {
+      if (!b->gexec || b->gticks != ticks) {
+        if (b->gexec) cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+        BCK(b, cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+        stdg_status s = STDG_OK;
+        for (int t = 0; t < ticks && s == STDG_OK; ++t) s = tick(b);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(b->st, &graph);
+        if (s != STDG_OK) {
+          if (graph) cudaGraphDestroy(graph);
+          return s;
+        }
+        BCK(b, ce);
+        const cudaError_t ie = cudaGraphInstantiate(&b->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        BCK(b, ie);
+        b->gticks = ticks;
+      }
+      BCK(b, cudaGraphLaunch(b->gexec, b->st));
+    } else {
+      for (int t = 0; t < ticks; ++t) {
+        stdg_status s = tick(b);
+        if (s != STDG_OK) return s;
+      }
+    }
+  }
   return refresh(b, working);
+}
+
+stdg_status stdg_batch_configure(stdg_batch* b, double share_quantum, int share_max_stride, int use_graphs,
+                                 int autotune) {
+  if (!b || !(share_quantum >= 0.0) || share_max_stride < 1) return STDG_ERR_INVALID_ARG;
+  b->share_quantum = share_quantum;
+  b->share_max_stride = share_max_stride;
+  b->use_graphs = use_graphs != 0;
+  b->autotune = autotune != 0;
+  b->dirty = true;
+  return STDG_OK;
 }
 
 stdg_status stdg_batch_run(stdg_batch* b, int max_ticks, int* working) {

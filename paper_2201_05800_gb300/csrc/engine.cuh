@@ -54,6 +54,7 @@ struct SlotBuf {
   int chunk_elems;  // elements per work item of the build / dot / update kernels
   size_t L;         // slab length nelem * s * nd * r
   int item0, nitems;  // this slot's work items in the chunk list (control reduction)
+  int stride, offset; // the slot takes part in tick t when (t + offset) % stride == 0
 };
 
 // Scalar solver state of one slot (FP64).
@@ -88,11 +89,19 @@ struct EngLaunch {
   SlotBuf* buf;
   SlotCtl* ctl;
   double* partials;  // kEngRows per chunk item
+  int* tick;         // tick counter (device), advanced by the last launch of a tick
 };
 
-// dot, control, update
-cudaError_t eng_generic_launch(const EngLaunch& L, cudaStream_t st);
+// Whether slot b takes part in the current tick (size-aware sharing: a slot much larger
+// than the sharing quantum advances only every stride-th tick).
+__device__ __forceinline__ bool eng_runs(const EngLaunch& L, const SlotBuf& b) {
+  return b.stride <= 1 || ((*L.tick + b.offset) % b.stride) == 0;
+}
+
+
 // U = 1 (x) uprev, U32 = (float) U for one slot
 cudaError_t eng_init_slot(const SlotBuf& b, cudaStream_t st);
+// the launches of one tick after the physics kernels (dot, control, update, tick counter)
+cudaError_t eng_tick_tail(const EngLaunch& L, cudaStream_t st);
 
 }  // namespace stdg

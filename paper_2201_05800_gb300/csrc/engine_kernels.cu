@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(kEngThreads) eng_dot_kernel(const __grid_const
     const int ph = L.ctl[item.slot].phase;
     if (ph != kPhResid && ph != kPhArnoldi && ph != kPhReorth) continue;
     const SlotBuf b = L.buf[item.slot];
+    if (!eng_runs(L, b)) continue;
     long long e0, e1;
     chunk_range(b, item.idx, &e0, &e1);
     const size_t blockvals = (size_t)b.s * b.nd * b.r;
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(kEngThreads) eng_control_kernel(const __grid_c
   SlotCtl& c = L.ctl[slot];
   const SlotBuf& b = L.buf[slot];
   const int ph = c.phase;
-  if (ph != kPhResid && ph != kPhArnoldi && ph != kPhReorth) {
+  if ((ph != kPhResid && ph != kPhArnoldi && ph != kPhReorth) || !eng_runs(L, b)) {
     if (lane == 0) c.upd = kUpdNone;
     return;
   }
@@ -301,6 +302,8 @@ __global__ void __launch_bounds__(kEngThreads) eng_update_kernel(const __grid_co
   }
 }
 
+__global__ void eng_tick_kernel(int* tick) { *tick += 1; }
+
 __global__ void eng_init_kernel(const SlotBuf b) {
   const int tnode = b.nd * b.r;
   const size_t total = (size_t)b.nelem * b.s * tnode;
@@ -316,12 +319,13 @@ __global__ void eng_init_kernel(const SlotBuf b) {
 
 }  // namespace
 
-cudaError_t eng_generic_launch(const EngLaunch& L, cudaStream_t st) {
+cudaError_t eng_tick_tail(const EngLaunch& L, cudaStream_t st) {
   if (L.n_active <= 0) return cudaSuccess;
   eng_dot_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
   const int warps_per_block = kEngThreads / 32;
   eng_control_kernel<<<(L.n_active + warps_per_block - 1) / warps_per_block, kEngThreads, 0, st>>>(L);
   eng_update_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
+  eng_tick_kernel<<<1, 1, 0, st>>>(L.tick);
   return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256) eng_op_kernel(const __grid_constant__ Eng
   const int n = *L.n_op_items;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const EngItem item = L.op_items[it];
-    if (L.ctl[item.slot].phase != want) continue;
+    if (L.ctl[item.slot].phase != want || !eng_runs(L, L.buf[item.slot])) continue;
     const OpArgs<T>* ga = eng_args<T>(L, item.slot);
     // one item list serves both precisions: skip tiles beyond this precision's tile count
     if ((long long)item.idx * ga->epb >= ga->nelem) continue;
@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(128) eng_build_kernel(const __grid_constant__ 
     const EngItem item = L.chunk_items[it];
     if (L.ctl[item.slot].phase != kPhResid) continue;
     const SlotBuf& b = L.buf[item.slot];
+    if (!eng_runs(L, b)) continue;
     const long long e0 = (long long)item.idx * b.chunk_elems;
     const long long e1 = e0 + b.chunk_elems < b.nelem ? e0 + b.chunk_elems : b.nelem;
     for (long long idx = e0 * b.nd + threadIdx.x; idx < e1 * b.nd; idx += blockDim.x)
@@ -61,23 +62,50 @@ inline cudaError_t eng_smem_attr(K kern, size_t smem) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// prepare = 1: only set the shared-memory attributes of the op kernels (outside any
+// stream capture); prepare = 0: launch build, residual and Jv kernels of one tick.
 template <int DIM, int EQ>
-cudaError_t eng_physics_inst(const EngLaunch& L, cudaStream_t st) {
-  if (L.n_active <= 0) return cudaSuccess;
-  eng_build_kernel<DIM, EQ><<<L.chunk_grid, 128, 0, st>>>(L);
+cudaError_t eng_physics_inst(const EngLaunch& L, cudaStream_t st, int prepare) {
   auto k64 = eng_op_kernel<DIM, EQ, double, kModeResidual>;
   auto k32 = eng_op_kernel<DIM, EQ, float, kModeJvExact>;
-  cudaError_t e = eng_smem_attr(k64, L.op_smem64);
-  if (e != cudaSuccess) return e;
-  e = eng_smem_attr(k32, L.op_smem32);
-  if (e != cudaSuccess) return e;
+  if (prepare) {
+    cudaError_t e = eng_smem_attr(k64, L.op_smem64);
+    if (e != cudaSuccess) return e;
+    return eng_smem_attr(k32, L.op_smem32);
+  }
+  if (L.n_active <= 0) return cudaSuccess;
+  eng_build_kernel<DIM, EQ><<<L.chunk_grid, 128, 0, st>>>(L);
   k64<<<L.op_grid, 256, L.op_smem64, st>>>(L, kPhResid);
   k32<<<L.op_grid, 256, L.op_smem32, st>>>(L, kPhArnoldi);
   return cudaGetLastError();
 }
 
-cudaError_t eng_physics_euler2(const EngLaunch& L, cudaStream_t st);
-cudaError_t eng_physics_burgers2(const EngLaunch& L, cudaStream_t st);
-cudaError_t eng_physics_advection(int dim, const EngLaunch& L, cudaStream_t st);
+// One launch of an op kernel alone on a slot with the given epb (autotuning): mode 0 the
+// FP64 residual, 1 the FP32 Jv, with the slot's arguments overridden by `a64` / `a32`.
+template <int DIM, int EQ>
+cudaError_t eng_op_probe_inst(int mode, const OpArgs<double>& a64, const OpArgs<float>& a32, cudaStream_t st) {
+  if (mode == 0) {
+    auto kern = st_operator_kernel<DIM, EQ, double, kModeResidual, kMaxN, kMaxS, false>;
+    const size_t smem = op_smem_bytes<DIM, Phys<EQ, DIM>::R, double, kModeResidual>(a64.n, a64.s, a64.epb);
+    cudaError_t e = eng_smem_attr(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)((a64.nelem + a64.epb - 1) / a64.epb), 256, smem, st>>>(a64);
+  } else {
+    auto kern = st_operator_kernel<DIM, EQ, float, kModeJvExact, kMaxN, kMaxS, false>;
+    const size_t smem = op_smem_bytes<DIM, Phys<EQ, DIM>::R, float, kModeJvExact>(a32.n, a32.s, a32.epb);
+    cudaError_t e = eng_smem_attr(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)((a32.nelem + a32.epb - 1) / a32.epb), 256, smem, st>>>(a32);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t eng_physics_euler2(const EngLaunch& L, cudaStream_t st, int prepare);
+cudaError_t eng_physics_burgers2(const EngLaunch& L, cudaStream_t st, int prepare);
+cudaError_t eng_physics_advection(int dim, const EngLaunch& L, cudaStream_t st, int prepare);
+cudaError_t eng_probe_euler2(int mode, const OpArgs<double>& a64, const OpArgs<float>& a32, cudaStream_t st);
+cudaError_t eng_probe_burgers2(int mode, const OpArgs<double>& a64, const OpArgs<float>& a32, cudaStream_t st);
+cudaError_t eng_probe_advection(int dim, int mode, const OpArgs<double>& a64, const OpArgs<float>& a32,
+                                cudaStream_t st);
 
 }  // namespace stdg

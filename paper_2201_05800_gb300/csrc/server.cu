@@ -65,6 +65,10 @@ struct stdg_server {
   // counters
   unsigned long long n_admitted = 0, n_done = 0, ticks = 0;
   int max_running = 0;
+  // batch scheduling knobs (applied by the worker before its next round)
+  bool cfg_dirty = false;
+  double share_quantum = 0.0;
+  int share_max_stride = 16, use_graphs = 1, autotune = 1;
 };
 
 namespace {
@@ -103,6 +107,10 @@ void worker_main(stdg_server* s) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
       if (s->stop) break;
+      if (s->cfg_dirty) {
+        stdg_batch_configure(s->batch, s->share_quantum, s->share_max_stride, s->use_graphs, s->autotune);
+        s->cfg_dirty = false;
+      }
       if (s->running.empty() && s->queue.empty())
         s->cv.wait_for(lk, std::chrono::milliseconds(50), [&] { return s->stop || !s->queue.empty(); });
       if (s->stop) break;
@@ -273,6 +281,18 @@ stdg_status stdg_server_poll(stdg_server* s, unsigned long long ticket, double w
     times[2] = seconds(r.t_submit, r.t_done);
   }
   s->reqs.erase(it);
+  return STDG_OK;
+}
+
+stdg_status stdg_server_configure(stdg_server* s, double share_quantum, int share_max_stride, int use_graphs,
+                                  int autotune) {
+  if (!s || !(share_quantum >= 0.0) || share_max_stride < 1) return STDG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->share_quantum = share_quantum;
+  s->share_max_stride = share_max_stride;
+  s->use_graphs = use_graphs;
+  s->autotune = autotune;
+  s->cfg_dirty = true;
   return STDG_OK;
 }
 

@@ -298,6 +298,8 @@ _BATCH_SIGS = {
 }
 _BATCH_SIGS.update({
     "stdg_batch_done_slots": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    "stdg_batch_configure": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "stdg_server_configure": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "stdg_server_create": (ctypes.c_int, [ctypes.POINTER(stdg_batch_desc), ctypes.c_int, ctypes.POINTER(_P)]),
     "stdg_server_destroy": (ctypes.c_int, [_P]),
     "stdg_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(stdg_config_desc), _P,
@@ -411,6 +413,11 @@ class Batch:
         self._check(self._lib.stdg_batch_remove(self._h, slot))
         self._descs.pop(slot, None)
 
+    def configure(self, share_quantum=0.0, share_max_stride=16, use_graphs=True, autotune=True):
+        """stdg_batch_configure: size-aware sharing, CUDA-graph ticks, tile autotuning."""
+        self._check(self._lib.stdg_batch_configure(self._h, float(share_quantum), int(share_max_stride),
+                                                   1 if use_graphs else 0, 1 if autotune else 0))
+
     def done_slots(self):
         """Slots that finished as of the last step/run and are not removed yet."""
         n = self._lib.stdg_batch_done_slots(self._h, None, 0)
@@ -484,6 +491,12 @@ class Server:
         self._lens.pop(ticket, None)
         return {"status": status.value, "stats": stats.as_dict(), "u": u, "queue_s": times[0],
                 "service_s": times[1], "latency_s": times[2]}
+
+    def configure(self, share_quantum=0.0, share_max_stride=16, use_graphs=True, autotune=True):
+        st = self._lib.stdg_server_configure(self._h, float(share_quantum), int(share_max_stride),
+                                             1 if use_graphs else 0, 1 if autotune else 0)
+        if st != 0:
+            raise StdgError(st, "stdg_server_configure failed")
 
     def counters(self):
         a, c, t = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0), ctypes.c_ulonglong(0)

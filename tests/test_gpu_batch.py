@@ -164,3 +164,25 @@ def test_viscous_burgers_mix_matches_oracle(S):
             U = p.from_ext(B.get_slab(slot))
             err = rel_lgl(p, U, _oracle(p, u0))
             assert err <= 1e-8, (p.cells, p.N, p.s, p.nu, err, st)
+
+
+def test_scheduling_knobs_keep_results(S):
+    """Size-aware sharing (a large slot advances every k-th tick) and graph replay change only
+    when slots advance: results are bitwise those of plain ticking.  Tile autotuning changes
+    the CTA tiling of the operator only: results agree to rounding."""
+    probs = [_vortex(*c) for c in EULER_MIX[:4]] + [_vortex((12, 10), 4, 4)]
+    results = {}
+    for name, kw in [("plain", dict(use_graphs=False, autotune=False)),
+                     ("graphs", dict(use_graphs=True, autotune=False)),
+                     ("shared", dict(share_quantum=2000.0, share_max_stride=8, use_graphs=True, autotune=False)),
+                     ("tuned", dict(use_graphs=True, autotune=True))]:
+        with S.Batch(2, S.EULER, 8, 256 << 20) as B:
+            B.configure(**kw)
+            slots = [B.add(p.config(**WORK), np.ascontiguousarray(u0).ravel()) for p, u0 in probs]
+            assert B.run(50000) == 0
+            results[name] = [(B.query(sl)[1], B.get_slab(sl)) for sl in slots]
+    for name in ("graphs", "shared"):
+        for (st0, U0), (st1, U1) in zip(results["plain"], results[name]):
+            assert st1 == st0 == 0 and np.array_equal(U0, U1), name
+    for (p, _), (_, U0), (st1, U1) in zip(probs, results["plain"], results["tuned"]):
+        assert st1 == 0 and rel_lgl(p, p.from_ext(U1), p.from_ext(U0)) <= 1e-9
