@@ -636,7 +636,7 @@ def _serving_leg(stdg, rates, n_req):
             "sequential": {"p50_ms": pct(seq_lat, 0.5), "p99_ms": pct(seq_lat, 0.99),
                            "solves_per_s": n_req / fin}}
     out["scheduling"] = {"share_quantum_dof": SERVE_SHARE_QUANTUM, "share_max_stride": SERVE_SHARE_MAX_STRIDE,
-                         "graphs": True, "autotune": True}
+                         "graphs": True, "autotune": False}
     out["sequential_path"] = ("stdg_advance_slab per request in arrival order (FP32 exact Jv, point-block "
                               "preconditioner); latencies from the measured service times under the same arrivals")
     out["sequential_statuses"] = {str(k): seq_status.count(k) for k in sorted(set(seq_status))}

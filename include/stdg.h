@@ -240,9 +240,14 @@ stdg_status stdg_slab_norm_noalloc(const double* x, size_t len, double* out, voi
  *   (stop: ||R||_2 <= max(newton_rtol ||R(U0)||_2, newton_atol)), each step
  *   solving J dU = -R by flexible GMRES(gmres_m) (no restart; the step takes
  *   the iterate after at most gmres_m iterations or at gmres_rtol), right-
- *   preconditioned by the point-block P (STDG_PRECOND_POINT_BLOCK), with FP32
- *   Krylov vectors and exact (forward-mode) FP32 Jacobian-vector products;
- *   then u^{n+1} = U^s.
+ *   preconditioned, with FP32 Krylov vectors and exact (forward-mode) FP32
+ *   Jacobian-vector products; then u^{n+1} = U^s.  Preconditioner: Euler and
+ *   inst->precond == STDG_PRECOND_POINT_BLOCK: the point-block P above;
+ *   otherwise (scalar equations) an element tensor-product inverse: the
+ *   temporal block together with the element-local interior penalty operator
+ *   and an upwind face dissipation with the slot's wave-speed bound (|a| for
+ *   advection, max |u0| for Burgers), applied exactly by fast diagonalisation
+ *   (1D eigenvectors along each direction, an s x s inverse per mode).
  * A slot's result does not depend on the other slots (no reduction crosses
  * slots, all reductions have a fixed order): bitwise the same alone or in a
  * mix.  Slot memory comes from one device arena of hbm_budget_bytes
@@ -284,7 +289,7 @@ stdg_status stdg_batch_remove(stdg_batch* b, int slot);
 /* Device bytes a problem would take in the arena (0 if invalid). */
 size_t stdg_batch_slot_bytes(const stdg_batch* b, const stdg_config_desc* inst);
 size_t stdg_batch_free_bytes(const stdg_batch* b);
-/* Scheduling knobs of a batch (defaults: 0, 16, 1, 1).
+/* Scheduling knobs of a batch (defaults: 0, 16, 1, 0).
  * share_quantum > 0 enables size-aware sharing: a slot of L space-time DOF
  *   takes part only in every k-th tick, k = clamp(round(L / share_quantum), 1,
  *   share_max_stride), so that very large slots do not set the tick time of
@@ -292,8 +297,10 @@ size_t stdg_batch_free_bytes(const stdg_batch* b);
  * use_graphs: each stdg_batch_step is replayed as one captured CUDA graph of
  *   its ticks (recaptured when the slot set or the tick count changes).
  * autotune: elements per CTA of the operator kernels chosen by timing the
- *   candidates on the first slot of each (dim, equation, N, s) class, cached
- *   for the process (every later slot of the class gets the same tiles). */
+ *   candidates on a virtual 4096-element grid of each (dim, equation, N, s)
+ *   class (the first time the class is admitted), cached for the process so
+ *   that every slot of a class gets the same tiles; otherwise the largest tile
+ *   of at most 256 nodes within 96 KB of shared memory. */
 stdg_status stdg_batch_configure(stdg_batch* b, double share_quantum, int share_max_stride, int use_graphs,
                                  int autotune);
 /* Slots that finished (as of the last step/run) and are not removed yet:

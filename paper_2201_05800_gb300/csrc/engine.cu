@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "args_host.cuh"
+#include "lgl_host.h"
 #include "engine.cuh"
 #include "engine_ops.cuh"
 #include "ops.h"
@@ -73,7 +74,7 @@ struct Layout {
   int n, s, nd, r, m, dim;
   long long nelem;
   size_t L, S, npinv;
-  size_t off_U, off_R, off_uprev, off_U32, off_Pinv, off_V, off_Z, bytes;
+  size_t off_U, off_R, off_uprev, off_U32, off_Pinv, off_V, off_Z, off_K, kfloats, bytes;
 };
 
 struct HostSlot {
@@ -119,8 +120,9 @@ struct stdg_batch {
   bool use_graphs = true;       // capture the ticks of a step as one CUDA graph
   cudaGraphExec_t gexec = nullptr;
   int gticks = 0;
-  bool autotune = true;         // pick elements per CTA of the op kernels by measurement
+  bool autotune = false;        // pick elements per CTA of the op kernels by measurement
   bool own_stream = false;      // created here when the caller passed the legacy default stream
+  bool any_kron = false;        // some active slot uses the element tensor-product preconditioner
 };
 
 namespace {
@@ -217,6 +219,9 @@ Layout layout_of(const stdg_config_desc* d) {
   o += align_up(l.L * 4 * (size_t)(l.m + 1));
   l.off_Z = o;
   o += align_up(l.L * 4 * (size_t)l.m);
+  l.off_K = o;
+  l.kfloats = (size_t)4 * l.n * l.n + (size_t)l.nd * l.s * l.s;
+  o += align_up(l.kfloats * 4);
   l.bytes = o;
   return l;
 }
@@ -261,6 +266,8 @@ cudaError_t probe(const stdg_batch* b, int mode, const OpArgs<double>& a64, cons
 stdg_status rebuild(stdg_batch* b) {
   std::vector<EngItem> op, ch;
   b->smem64 = b->smem32 = 0;
+  b->any_kron = false;
+  for (int id : b->active) b->any_kron = b->any_kron || b->slots[id].buf.kron;
   for (int id : b->active) {
     HostSlot& hs = b->slots[id];
     const Layout& l = hs.lay;
@@ -345,6 +352,7 @@ stdg_status tick(stdg_batch* b) {
   L.ctl = b->ctl;
   L.partials = b->partials;
   L.tick = b->tick_d;
+  L.any_kron = b->any_kron ? 1 : 0;
   cudaError_t e = physics(b, L, 0);
   if (e != cudaSuccess) return bfail(b, STDG_ERR_CUDA, std::string("engine physics launch: ") + cudaGetErrorString(e));
   e = eng_tick_tail(L, b->st);
@@ -382,10 +390,152 @@ stdg_status refresh(stdg_batch* b, int* working) {
   return STDG_OK;
 }
 
-// Elements per CTA of the two op kernels for the slot's class: cached, else measured on the
-// new slot's own data (U = 1 (x) u^n; outputs into R and the unused basis row V_1).
+// Eigen-decomposition of a symmetric n x n matrix S (row major, destroyed) by cyclic Jacobi
+// rotations (Golub and Van Loan, Sec. 8.5): S = Q diag(lam) Q^T, Q row major.
+void sym_eig(int n, double* S, double* Q, double* lam) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Q[i * n + j] = i == j ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) (i == j ? diag : off) += S[i * n + j] * S[i * n + j];
+    if (off <= 1e-30 * diag) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = S[p * n + q];
+        if (apq == 0.0) continue;
+        const double theta = (S[q * n + q] - S[p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < n; ++k) {  // S <- S J
+          const double skp = S[k * n + p], skq = S[k * n + q];
+          S[k * n + p] = c * skp - sn * skq;
+          S[k * n + q] = sn * skp + c * skq;
+        }
+        for (int k = 0; k < n; ++k) {  // S <- J^T S
+          const double spk = S[p * n + k], sqk = S[q * n + k];
+          S[p * n + k] = c * spk - sn * sqk;
+          S[q * n + k] = sn * spk + c * sqk;
+        }
+        for (int k = 0; k < n; ++k) {  // Q <- Q J
+          const double qkp = Q[k * n + p], qkq = Q[k * n + q];
+          Q[k * n + p] = c * qkp - sn * qkq;
+          Q[k * n + q] = sn * qkp + c * qkq;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) lam[i] = S[i * n + i];
+}
+
+// Inverse of an s x s matrix (row major) by Gauss-Jordan with partial pivoting.
+void small_inverse(int s, const double* A, double* Ai) {
+  double W[kMaxS][2 * kMaxS];
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) {
+      W[i][j] = A[i * s + j];
+      W[i][s + j] = i == j ? 1.0 : 0.0;
+    }
+  for (int c = 0; c < s; ++c) {
+    int pv = c;
+    for (int q = c + 1; q < s; ++q)
+      if (std::fabs(W[q][c]) > std::fabs(W[pv][c])) pv = q;
+    for (int j = 0; j < 2 * s; ++j) std::swap(W[c][j], W[pv][j]);
+    const double inv = 1.0 / W[c][c];
+    for (int j = 0; j < 2 * s; ++j) W[c][j] *= inv;
+    for (int q = 0; q < s; ++q)
+      if (q != c) {
+        const double f = W[q][c];
+        for (int j = 0; j < 2 * s; ++j) W[q][j] -= f * W[c][j];
+      }
+  }
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) Ai[i * s + j] = W[i][s + j];
+}
+
+// Data of the element tensor-product preconditioner of a scalar slot (see eng_kron_kernel):
+// the element-local 1D operators A_a (interior penalty form with the neighbours zero, plus
+// the upwind dissipation lambda_a/(h_a w_end) at both end nodes, lambda_a the slot's wave
+// speed bound), their eigen-decompositions (A_a = W^-1 K_a with K_a symmetric, so
+// A_a = V Lambda V^-1, V = W^-1/2 Q, V^-1 = Q^T W^1/2) and P_k^-1 = (T - dt/2 Lambda_k M_tau)^-1
+// for every mode k of the element.
+std::vector<float> kron_data(const stdg_config_desc* d, int n, int s, int nd, const double lam[3]) {
+  const int N = n - 1, dim = d->dim;
+  double xi[16], w[16], D[256], tau[16], om[16], Dt[256];
+  lgl_rule(n, xi, w);
+  diff_matrix(n, xi, D);
+  lgl_rule(s, tau, om);
+  diff_matrix(s, tau, Dt);
+  const double nu = d->viscosity;
+  const double eta = d->penalty > 0.0 ? d->penalty : 10.0 * N * N;
+  std::vector<double> V[2], Vi[2], lm[2];
+  for (int a = 0; a < 2; ++a) {
+    V[a].assign(n * n, 0.0);
+    Vi[a].assign(n * n, 0.0);
+    lm[a].assign(n, 0.0);
+    for (int i = 0; i < n; ++i) V[a][i * n + i] = Vi[a][i * n + i] = 1.0;
+    if (a >= dim) continue;
+    const double h = (d->hi[a] - d->lo[a]) / d->cells[a], g = 2.0 / h, sig = nu * eta / h;
+    std::vector<double> A(n * n, 0.0);
+    for (int i = 0; i < n; ++i) {  // column i: response to the unit vector e_i
+      std::vector<double> q(n), B(n, 0.0);
+      for (int k = 0; k < n; ++k) q[k] = g * D[k * n + i];
+      for (int ip = 0; ip < n; ++ip) {
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) acc += w[k] * D[k * n + ip] * q[k];
+        B[ip] = nu * g / w[ip] * acc;
+      }
+      const double jup = i == N ? 1.0 : 0.0, jlo = i == 0 ? -1.0 : 0.0;
+      B[N] += g / w[N] * (-nu * 0.5 * q[N] + sig * jup);
+      B[0] += g / w[0] * (nu * 0.5 * q[0] - sig * jlo);
+      for (int ip = 0; ip < n; ++ip) B[ip] -= g / w[ip] * nu * 0.5 * g * (D[N * n + ip] * jup + D[ip] * jlo);
+      if (i == N) B[N] += 0.5 * g / w[N] * lam[a];
+      if (i == 0) B[0] += 0.5 * g / w[0] * lam[a];
+      for (int ip = 0; ip < n; ++ip) A[ip * n + i] = B[ip];
+    }
+    std::vector<double> S(n * n), Q(n * n);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double sij = std::sqrt(w[i]) * A[i * n + j] / std::sqrt(w[j]);
+        const double sji = std::sqrt(w[j]) * A[j * n + i] / std::sqrt(w[i]);
+        S[i * n + j] = 0.5 * (sij + sji);
+      }
+    sym_eig(n, S.data(), Q.data(), lm[a].data());
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < n; ++k) {
+        V[a][i * n + k] = Q[i * n + k] / std::sqrt(w[i]);
+        Vi[a][k * n + i] = Q[i * n + k] * std::sqrt(w[i]);
+      }
+  }
+  std::vector<float> out((size_t)4 * n * n + (size_t)nd * s * s);
+  for (int i = 0; i < n * n; ++i) {
+    out[i] = (float)Vi[0][i];
+    out[n * n + i] = (float)V[0][i];
+    out[2 * n * n + i] = (float)Vi[1][i];
+    out[3 * n * n + i] = (float)V[1][i];
+  }
+  std::vector<double> P(s * s), Pi(s * s);
+  for (int k = 0; k < nd; ++k) {
+    const double Lk = lm[0][k % n] + (dim > 1 ? lm[1][(k / n) % n] : 0.0);
+    for (int m = 0; m < s; ++m)
+      for (int j = 0; j < s; ++j) {
+        double v = om[j] * Dt[j * s + m];  // (D_tau^T M_tau)[m][j]
+        if (m == s - 1 && j == s - 1) v -= 1.0;
+        if (m == j) v -= 0.5 * d->dt * Lk * om[m];
+        P[m * s + j] = v;
+      }
+    small_inverse(s, P.data(), Pi.data());
+    for (int q = 0; q < s * s; ++q) out[(size_t)4 * n * n + (size_t)k * s * s + q] = (float)Pi[q];
+  }
+  return out;
+}
+
+// Elements per CTA of the two op kernels for the slot's class: cached, else measured.  The
+// probe is a virtual periodic grid of the class with at least 4096 elements (enough CTAs to
+// fill the GPU, as in a loaded batch) holding a uniform state; each candidate tile is timed
+// over three launches after a warm-up, and the fastest kept (the smaller tile unless the
+// larger is more than 3% faster).
 stdg_status tune(stdg_batch* b, const Layout& l, int eq, const OpArgs<double>& k64, const OpArgs<float>& k32,
-                 const SlotBuf& sb, int* epb64, int* epb32) {
+                 int* epb64, int* epb32) {
   const TuneKey key{l.dim, eq, l.n, l.s};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -397,45 +547,79 @@ stdg_status tune(stdg_batch* b, const Layout& l, int eq, const OpArgs<double>& k
     }
   }
   const int r = ncomp(eq, l.dim);
-  const int maxe = (int)std::min<long long>(std::max(1, 256 / l.nd), l.nelem);
-  const int cand[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 24, 28, 32};
-  cudaEvent_t e0, e1;
-  BCK(b, cudaEventCreate(&e0));
-  BCK(b, cudaEventCreate(&e1));
+  const int side = l.dim == 1 ? 4096 : 64;
+  const long long nel = l.dim == 1 ? 4096 : 4096;
+  const size_t S = (size_t)nel * l.nd * r, L = S * l.s;
+  double *U = nullptr, *R = nullptr, *up = nullptr;
+  float *U32 = nullptr, *O32 = nullptr;
+  bool ok = cudaMalloc(&U, L * 8) == cudaSuccess && cudaMalloc(&R, L * 8) == cudaSuccess &&
+            cudaMalloc(&up, S * 8) == cudaSuccess && cudaMalloc(&U32, L * 4) == cudaSuccess &&
+            cudaMalloc(&O32, L * 4) == cudaSuccess;
+  Fill5 st;
+  if (eq == STDG_EULER) {
+    const double rho = 1.0, v = 0.5, p = 1.0;
+    st.v[0] = rho;
+    for (int a = 0; a < l.dim; ++a) st.v[1 + a] = rho * v;
+    st.v[r - 1] = p / (k64.gamma - 1.0) + 0.5 * rho * v * v * l.dim;
+  } else {
+    st.v[0] = 0.3;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ok = ok && eng_fill_state(U, U32, L, r, st, b->st) == cudaSuccess &&
+       cudaMemcpyAsync(up, U, S * 8, cudaMemcpyDeviceToDevice, b->st) == cudaSuccess &&
+       cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
   int best[2] = {*epb64, *epb32};
-  for (int mode = 0; mode < 2; ++mode) {
-    float best_ms = 1e30f;
-    for (int c : cand) {
-      if (c > maxe) break;
-      if (operator_smem_bytes(l.dim, r, mode == 0 ? 8 : 4, mode == 0 ? kModeResidual : kModeJvExact, l.n, l.s, c) >
-          kOpSmemCap)
-        break;
-      OpArgs<double> a = k64;
-      OpArgs<float> f = k32;
-      a.epb = c;
-      a.out = sb.R;
-      f.epb = c;
-      f.U = sb.U32;
-      f.v = sb.U32;
-      f.out = sb.V + l.L;
-      float ms_min = 1e30f;
-      for (int rep = 0; rep < 3; ++rep) {
-        BCK(b, cudaEventRecord(e0, b->st));
-        BCK(b, probe(b, mode, a, f));
-        BCK(b, cudaEventRecord(e1, b->st));
-        BCK(b, cudaEventSynchronize(e1));
-        float ms = 0.f;
-        BCK(b, cudaEventElapsedTime(&ms, e0, e1));
-        if (rep > 0) ms_min = std::min(ms_min, ms);  // first launch warms up
-      }
-      if (ms_min < best_ms * 0.97f) {  // prefer the smaller tile unless clearly faster
-        best_ms = ms_min;
-        best[mode] = c;
+  if (ok) {
+    const int maxe = std::max(1, 256 / l.nd);
+    const int cand[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 24, 28, 32};
+    for (int mode = 0; mode < 2 && ok; ++mode) {
+      float best_ms = 1e30f;
+      for (int c : cand) {
+        if (c > maxe) break;
+        if (operator_smem_bytes(l.dim, r, mode == 0 ? 8 : 4, mode == 0 ? kModeResidual : kModeJvExact, l.n, l.s,
+                                c) > kOpSmemCap)
+          break;
+        OpArgs<double> a = k64;
+        OpArgs<float> f = k32;
+        a.K[0] = f.K[0] = l.dim == 1 ? (int)nel : side;
+        a.K[1] = f.K[1] = l.dim == 1 ? 1 : side;
+        a.K[2] = f.K[2] = 1;
+        a.nelem = f.nelem = nel;
+        a.epb = f.epb = c;
+        a.U = U;
+        a.uprev = up;
+        a.out = R;
+        a.fout = nullptr;
+        f.U = U32;
+        f.v = U32;
+        f.out = O32;
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 4 && ok; ++rep) {
+          ok = cudaEventRecord(e0, b->st) == cudaSuccess && probe(b, mode, a, f) == cudaSuccess &&
+               cudaEventRecord(e1, b->st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+          float ms = 0.f;
+          if (ok) cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) ms_min = std::min(ms_min, ms);  // the first launch warms up
+        }
+        if (ms_min < best_ms * 0.97f) {
+          best_ms = ms_min;
+          best[mode] = c;
+        }
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(U);
+  cudaFree(R);
+  cudaFree(up);
+  cudaFree(U32);
+  cudaFree(O32);
+  if (!ok) {
+    cudaGetLastError();
+    return bfail(b, STDG_ERR_CUDA, "tile probing failed");
+  }
+  // a tile larger than the slot is clipped by the slot (fewer elements than one tile)
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto ins = g_tune.emplace(key, std::make_pair(best[0], best[1]));
   *epb64 = ins.first->second.first;
@@ -567,6 +751,29 @@ stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* d, const doubl
   sb.chunk_elems = std::max(1, (int)(kChunkValues / ((size_t)l.s * l.nd * l.r)));
   sb.nitems = (int)((l.nelem + sb.chunk_elems - 1) / sb.chunk_elems);
   sb.item0 = 0;
+  sb.dim = l.dim;
+  sb.n = l.n;
+  sb.kron = (d->equation != STDG_EULER && d->precond != STDG_PRECOND_POINT_BLOCK) ? 1 : 0;
+  sb.kdat = reinterpret_cast<const float*>(base + l.off_K);
+  if (sb.kron) {
+    double lam[3] = {0.0, 0.0, 0.0};
+    if (d->equation == STDG_ADVECTION) {
+      for (int a = 0; a < 3; ++a) lam[a] = std::fabs(d->adv_vel[a]);
+    } else {  // Burgers: the largest |u| of the initial state bounds the wave speed
+      std::vector<double> hu;
+      const double* u = u0;
+      if (kind == STDG_DEVICE) {
+        hu.resize(l.S);
+        BCK(b, cudaMemcpy(hu.data(), u0, l.S * sizeof(double), cudaMemcpyDeviceToHost));
+        u = hu.data();
+      }
+      double mx = 0.0;
+      for (size_t i = 0; i < l.S; ++i) mx = std::max(mx, std::fabs(u[i]));
+      lam[0] = lam[1] = lam[2] = mx;
+    }
+    std::vector<float> kd = kron_data(d, l.n, l.s, l.nd, lam);
+    BCK(b, cudaMemcpy(base + l.off_K, kd.data(), kd.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
   hs.epb64 = pick_epb(l.dim, d->equation, 8, kModeResidual, l.n, l.s, l.nelem, l.nd);
   hs.epb32 = pick_epb(l.dim, d->equation, 4, kModeJvExact, l.n, l.s, l.nelem, l.nd);
   // operator constants
@@ -603,8 +810,10 @@ stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* d, const doubl
                          kind == STDG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, b->st));
   BCK(b, eng_init_slot(sb, b->st));
   if (b->autotune) {
-    stdg_status ts = tune(b, l, d->equation, k64, k32, sb, &hs.epb64, &hs.epb32);
+    stdg_status ts = tune(b, l, d->equation, k64, k32, &hs.epb64, &hs.epb32);
     if (ts != STDG_OK) return ts;
+    hs.epb64 = (int)std::min<long long>(hs.epb64, l.nelem);
+    hs.epb32 = (int)std::min<long long>(hs.epb32, l.nelem);
     k64.epb = hs.epb64;
     k32.epb = hs.epb32;
     BCK(b, cudaMemcpyAsync(b->a64 + id, &k64, sizeof(k64), cudaMemcpyHostToDevice, b->st));

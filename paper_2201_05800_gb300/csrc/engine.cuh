@@ -55,6 +55,10 @@ struct SlotBuf {
   size_t L;         // slab length nelem * s * nd * r
   int item0, nitems;  // this slot's work items in the chunk list (control reduction)
   int stride, offset; // the slot takes part in tick t when (t + offset) % stride == 0
+  // element tensor-product preconditioner (scalar equations; kron = 1), see eng_kron_kernel:
+  // kdat = [Vx^-1 | Vx | Vy^-1 | Vy] (n x n each) then P_k^-1 (s x s) per mode k of the element
+  int kron, dim, n;
+  const float* kdat;
 };
 
 // Scalar solver state of one slot (FP64).
@@ -90,6 +94,7 @@ struct EngLaunch {
   SlotCtl* ctl;
   double* partials;  // kEngRows per chunk item
   int* tick;         // tick counter (device), advanced by the last launch of a tick
+  int any_kron;      // some slot uses the element tensor-product preconditioner
 };
 
 // Whether slot b takes part in the current tick (size-aware sharing: a slot much larger
@@ -101,6 +106,11 @@ __device__ __forceinline__ bool eng_runs(const EngLaunch& L, const SlotBuf& b) {
 
 // U = 1 (x) uprev, U32 = (float) U for one slot
 cudaError_t eng_init_slot(const SlotBuf& b, cudaStream_t st);
+// U[i] = U32[i] = state.v[i % r] (a uniform state for tile probing)
+struct Fill5 {
+  double v[5];
+};
+cudaError_t eng_fill_state(double* U, float* U32, size_t L, int r, const Fill5& state, cudaStream_t st);
 // the launches of one tick after the physics kernels (dot, control, update, tick counter)
 cudaError_t eng_tick_tail(const EngLaunch& L, cudaStream_t st);
 

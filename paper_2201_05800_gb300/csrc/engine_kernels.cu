@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kEngThreads) eng_update_kernel(const __grid_co
       } else if (mode == kUpdExtract) {
         b.uprev[e * tnode + q] = b.U[base + (size_t)(s - 1) * tnode];
       }
-      if (apply_z) {
+      if (apply_z && !b.kron) {  // Kron slots: z is formed by eng_kron_kernel
         const float* P = b.Pinv + (e * s * s) * nd + node;
         for (int m = 0; m < s; ++m) {
           float z = 0.f;
@@ -302,7 +302,113 @@ __global__ void __launch_bounds__(kEngThreads) eng_update_kernel(const __grid_co
   }
 }
 
+// z = P^-1 (zscale w) with the element tensor-product preconditioner of scalar
+// equations.  Per element, with A_a the element-local 1D operator along e_a (the
+// interior penalty form with the neighbours set to zero, plus the upwind
+// dissipation lambda/(h_a w_end) at the end nodes), A_a = V_a Lambda_a V_a^-1:
+//   P = T (x) I - dt/2 M_tau (x) (A_x (+) A_y)
+//     = (I (x) V_y (x) V_x) [block-diag over modes k: P_k = T - dt/2 Lambda_k M_tau]
+//       (I (x) V_y^-1 (x) V_x^-1),
+// so z is three contractions: V^-1 along x and y, P_k^-1 (s x s) per mode, V back.
+// The elements of a chunk are processed in groups held in shared memory.
+__global__ void __launch_bounds__(kEngThreads) eng_kron_kernel(const __grid_constant__ EngLaunch L) {
+  constexpr int kBuf = 2048;  // floats per ping-pong buffer
+  __shared__ float sa[kBuf], sb2[kBuf];
+  const int nitems = *L.n_chunk_items;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const EngItem item = L.chunk_items[it];
+    const SlotBuf b = L.buf[item.slot];
+    if (!b.kron) continue;
+    const SlotCtl& c = L.ctl[item.slot];
+    const int mode = c.upd;
+    if (mode != kUpdInit && mode != kUpdGSZ) continue;
+    const int row = mode == kUpdInit ? 0 : c.upd_row;
+    const float zs = (float)c.zscale;
+    const float* src = b.V + (size_t)row * b.L;
+    float* dst = b.Z + (size_t)row * b.L;
+    const int n = b.n, s = b.s, nd = b.nd, dim = b.dim;
+    const int per = s * nd;  // values of one element (r = 1)
+    const int E = kBuf / per > 0 ? kBuf / per : 1;
+    const float* Vxi = b.kdat;
+    const float* Vx = Vxi + n * n;
+    const float* Vyi = Vx + n * n;
+    const float* Vy = Vyi + n * n;
+    const float* Pk = Vy + n * n;
+    long long e0, e1;
+    chunk_range(b, item.idx, &e0, &e1);
+    for (long long eg = e0; eg < e1; eg += E) {
+      const int ne = (int)((e1 - eg) < E ? (e1 - eg) : E);
+      const int tot = ne * per;
+      for (int t = threadIdx.x; t < tot; t += blockDim.x) sa[t] = zs * src[(size_t)eg * per + t];
+      __syncthreads();
+      // forward along x: sb2[., iy, kx] = sum_ix Vx^-1[kx][ix] sa[., iy, ix]
+      for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        const int kx = t % n, base = t - kx;
+        float acc = 0.f;
+        for (int ix = 0; ix < n; ++ix) acc = fmaf(Vxi[kx * n + ix], sa[base + ix], acc);
+        sb2[t] = acc;
+      }
+      __syncthreads();
+      const float* cur = sb2;
+      float* nxt = sa;
+      if (dim == 2) {  // forward along y
+        for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+          const int kx = t % n, ky = (t / n) % n, base = t - (t % nd);
+          float acc = 0.f;
+          for (int iy = 0; iy < n; ++iy) acc = fmaf(Vyi[ky * n + iy], cur[base + iy * n + kx], acc);
+          nxt[t] = acc;
+        }
+        __syncthreads();
+        cur = sa;
+        nxt = sb2;
+      }
+      // per mode k: z_m = sum_j (P_k^-1)[m][j] y_j
+      for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        const int k = t % nd, m = (t / nd) % s, el = t / per;
+        const float* P = Pk + ((size_t)k * s + m) * s;
+        float acc = 0.f;
+        for (int j = 0; j < s; ++j) acc = fmaf(P[j], cur[el * per + j * nd + k], acc);
+        nxt[t] = acc;
+      }
+      __syncthreads();
+      {
+        const float* c2 = nxt;
+        float* n2 = const_cast<float*>(cur);
+        if (dim == 2) {  // back along y: n2[., iy, kx] = sum_ky Vy[iy][ky] c2[., ky, kx]
+          for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+            const int kx = t % n, iy = (t / n) % n, base = t - (t % nd);
+            float acc = 0.f;
+            for (int ky = 0; ky < n; ++ky) acc = fmaf(Vy[iy * n + ky], c2[base + ky * n + kx], acc);
+            n2[t] = acc;
+          }
+          __syncthreads();
+          const float* tmp = c2;
+          c2 = n2;
+          n2 = const_cast<float*>(tmp);
+        }
+        // back along x, straight to global memory
+        for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+          const int ix = t % n, base = t - ix;
+          float acc = 0.f;
+          for (int kx = 0; kx < n; ++kx) acc = fmaf(Vx[ix * n + kx], c2[base + kx], acc);
+          dst[(size_t)eg * per + t] = acc;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 __global__ void eng_tick_kernel(int* tick) { *tick += 1; }
+
+__global__ void eng_fill_kernel(double* U, float* U32, size_t L, int r, Fill5 st) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += stride) {
+    const double v = st.v[i % r];
+    U[i] = v;
+    U32[i] = (float)v;
+  }
+}
 
 __global__ void eng_init_kernel(const SlotBuf b) {
   const int tnode = b.nd * b.r;
@@ -325,7 +431,15 @@ cudaError_t eng_tick_tail(const EngLaunch& L, cudaStream_t st) {
   const int warps_per_block = kEngThreads / 32;
   eng_control_kernel<<<(L.n_active + warps_per_block - 1) / warps_per_block, kEngThreads, 0, st>>>(L);
   eng_update_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
+  if (L.any_kron) eng_kron_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
   eng_tick_kernel<<<1, 1, 0, st>>>(L.tick);
+  return cudaGetLastError();
+}
+
+cudaError_t eng_fill_state(double* U, float* U32, size_t L, int r, const Fill5& state, cudaStream_t st) {
+  size_t blocks = (L + 255) / 256;
+  if (blocks > 2432) blocks = 2432;
+  eng_fill_kernel<<<(unsigned)(blocks ? blocks : 1), 256, 0, st>>>(U, U32, L, r, state);
   return cudaGetLastError();
 }
 

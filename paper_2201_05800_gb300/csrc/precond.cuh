@@ -29,8 +29,10 @@ namespace stdg {
 // One (element, spatial node) idx = e * nd + node:  sigma_{I,m} from the wave speeds
 // lambda = max(|v_a| + c) over the two traces of every face through I, then
 // P_I by Gauss-Jordan elimination with partial pivoting (s <= 5).
-template <int DIM, int EQ, class TP>
-__device__ __forceinline__ void pb_build_node(const OpArgs<double>& k, const double* __restrict__ U,
+// CT: the arithmetic type (double for the FP64 solver; float for the FP32 Krylov solves,
+// where P^-1 is stored in FP32 anyway and FP64 operations are 64x slower).
+template <int DIM, int EQ, class TP, class CT = double>
+__device__ __forceinline__ void pb_build_node(const OpArgs<CT>& k, const double* __restrict__ U,
                                               TP* __restrict__ Pinv, long long idx) {
   using P = Phys<EQ, DIM>;
   constexpr int R = P::R;
@@ -40,13 +42,13 @@ __device__ __forceinline__ void pb_build_node(const OpArgs<double>& k, const dou
   const int strides[3] = {1, n, n * n};
   const int ia[3] = {node % n, (node / n) % n, node / (n * n)};
   const long long ec[3] = {e % k.K[0], (e / k.K[0]) % k.K[1], e / ((long long)k.K[0] * k.K[1])};
-  double sig[kMaxS];
+  CT sig[kMaxS];
   for (int m = 0; m < s; ++m) {
-    double uo[R];
+    CT uo[R];
     const size_t go = (((size_t)e * s + m) * nd + node) * R;
 #pragma unroll
-    for (int c = 0; c < R; ++c) uo[c] = U[go + c];
-    double acc = 0.0;
+    for (int c = 0; c < R; ++c) uo[c] = (CT)U[go + c];
+    CT acc = CT(0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const bool up = ia[a] == n - 1, lo = ia[a] == 0;
@@ -58,27 +60,27 @@ __device__ __forceinline__ void pb_build_node(const OpArgs<double>& k, const dou
       const long long enb = (en[2] * k.K[1] + en[1]) * k.K[0] + en[0];
       const int nb_node = node + ((up ? 0 : n - 1) - ia[a]) * strides[a];
       const size_t gn = (((size_t)enb * s + m) * nd + nb_node) * R;
-      double un[R];
+      CT un[R];
 #pragma unroll
-      for (int c = 0; c < R; ++c) un[c] = U[gn + c];
-      const double lo_s = P::template speed<double, double>(uo, a, k);
-      const double nb_s = P::template speed<double, double>(un, a, k);
-      acc += 0.5 * k.ginv[a] * k.winv_end * (lo_s >= nb_s ? lo_s : nb_s);
+      for (int c = 0; c < R; ++c) un[c] = (CT)U[gn + c];
+      const CT lo_s = P::template speed<CT, CT>(uo, a, k);
+      const CT nb_s = P::template speed<CT, CT>(un, a, k);
+      acc += CT(0.5) * k.ginv[a] * k.winv_end * (lo_s >= nb_s ? lo_s : nb_s);
     }
     // viscous term: its diagonal is independent of U
-    if (k.nu != 0.0)
+    if (k.nu != CT(0))
       for (int a = 0; a < DIM; ++a) acc += k.vdiag[a][ia[a]];
     sig[m] = acc;
   }
   // augmented [P | I], row m = temporal node m
-  double A[kMaxS][2 * kMaxS];
+  CT A[kMaxS][2 * kMaxS];
   for (int m = 0; m < s; ++m) {
     for (int j = 0; j < s; ++j) {
-      double v = k.C[j][m];
+      CT v = k.C[j][m];
       if (m == j) v -= k.half_dt * k.omega[m] * sig[m];
-      if (m == s - 1 && j == s - 1) v -= 1.0;
+      if (m == s - 1 && j == s - 1) v -= CT(1);
       A[m][j] = v;
-      A[m][s + j] = (m == j) ? 1.0 : 0.0;
+      A[m][s + j] = (m == j) ? CT(1) : CT(0);
     }
   }
   for (int col = 0; col < s; ++col) {
@@ -87,16 +89,16 @@ __device__ __forceinline__ void pb_build_node(const OpArgs<double>& k, const dou
       if (fabs(A[q][col]) > fabs(A[piv][col])) piv = q;
     if (piv != col)
       for (int j = 0; j < 2 * s; ++j) {
-        const double t = A[col][j];
+        const CT t = A[col][j];
         A[col][j] = A[piv][j];
         A[piv][j] = t;
       }
-    const double inv = 1.0 / A[col][col];
+    const CT inv = CT(1) / A[col][col];
     for (int j = 0; j < 2 * s; ++j) A[col][j] *= inv;
     for (int q = 0; q < s; ++q) {
       if (q == col) continue;
-      const double f = A[q][col];
-      if (f != 0.0)
+      const CT f = A[q][col];
+      if (f != CT(0))
         for (int j = 0; j < 2 * s; ++j) A[q][j] -= f * A[col][j];
     }
   }

@@ -68,7 +68,7 @@ struct stdg_server {
   // batch scheduling knobs (applied by the worker before its next round)
   bool cfg_dirty = false;
   double share_quantum = 0.0;
-  int share_max_stride = 16, use_graphs = 1, autotune = 1;
+  int share_max_stride = 16, use_graphs = 1, autotune = 0;
 };
 
 namespace {

@@ -413,7 +413,7 @@ class Batch:
         self._check(self._lib.stdg_batch_remove(self._h, slot))
         self._descs.pop(slot, None)
 
-    def configure(self, share_quantum=0.0, share_max_stride=16, use_graphs=True, autotune=True):
+    def configure(self, share_quantum=0.0, share_max_stride=16, use_graphs=True, autotune=False):
         """stdg_batch_configure: size-aware sharing, CUDA-graph ticks, tile autotuning."""
         self._check(self._lib.stdg_batch_configure(self._h, float(share_quantum), int(share_max_stride),
                                                    1 if use_graphs else 0, 1 if autotune else 0))
@@ -492,7 +492,7 @@ class Server:
         return {"status": status.value, "stats": stats.as_dict(), "u": u, "queue_s": times[0],
                 "service_s": times[1], "latency_s": times[2]}
 
-    def configure(self, share_quantum=0.0, share_max_stride=16, use_graphs=True, autotune=True):
+    def configure(self, share_quantum=0.0, share_max_stride=16, use_graphs=True, autotune=False):
         st = self._lib.stdg_server_configure(self._h, float(share_quantum), int(share_max_stride),
                                              1 if use_graphs else 0, 1 if autotune else 0)
         if st != 0:
