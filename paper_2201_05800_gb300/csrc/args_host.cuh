@@ -49,6 +49,9 @@ inline void fill_op_args(OpArgs<T>& k, int dim, int n, int s, const int cells[3]
   for (int a = 0; a < 3; ++a) k.adv[a] = (T)adv[a];
   k.vscale = (T)1;
   for (int m = 0; m < s; ++m) k.inv_omega[m] = (T)(1.0 / om[m]);
+  k.mg_n = fast_div_magic((unsigned)n);
+  k.mg_n2 = fast_div_magic((unsigned)(n * n));
+  k.mg_nd = fast_div_magic((unsigned)nd);
   k.nu = (T)nu;
   if (nu > 0.0) {
     const int N = n - 1;

@@ -54,6 +54,8 @@ struct OpArgs {
   T vup[3][kMaxN];         // nu/2 (2/h_a)^2 D[N][i] / w_i: lift of the upper-face jump
   T vlo[3][kMaxN];         // nu/2 (2/h_a)^2 D[0][i] / w_i: lift of the lower-face jump
   T vdiag[3][kMaxN];       // diagonal of the viscous term of F per direction (preconditioner)
+  // multipliers for division by n, n^2 and n^d (fast_div; 0 for a divisor of 1)
+  unsigned mg_n, mg_n2, mg_nd;
   const T* U;              // slab, [e][m][node][c]
   const T* v;              // direction, same layout
   const T* F0;             // F(U), same layout (kModeJvFD)
@@ -61,6 +63,14 @@ struct OpArgs {
   T* out;                  // R or Jv (may be null in kModeResidual)
   T* fout;                 // F(U) (kModeResidual, may be null)
 };
+
+// Division of a small index by a runtime divisor d without an integer divide:
+// q = floor(t * ceil(2^32 / d) / 2^32) is exact for t, d < 2^16 (the error term
+// t (m d - 2^32) / 2^32 stays below 1).  mg = 0 encodes d = 1.
+__host__ __device__ inline unsigned fast_div_magic(unsigned d) {
+  return d <= 1 ? 0u : (unsigned)(((1ull << 32) + d - 1) / d);
+}
+__device__ __forceinline__ int fast_div(int t, unsigned mg) { return mg ? (int)__umulhi((unsigned)t, mg) : t; }
 
 // ---------------------------------------------------------------- dual numbers
 template <class T>

@@ -21,12 +21,66 @@ __device__ __forceinline__ void chunk_range(const SlotBuf& b, int idx, long long
   *e1 = hi < b.nelem ? hi : b.nelem;
 }
 
+// Block sum of k per-thread FP64 values into partials[0..k) (fixed order).
+template <int KB>
+__device__ __forceinline__ void block_reduce_store(const double (&accd)[KB], int k, double (*red)[kEngRows],
+                                                   double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < KB; ++i) {
+    if (i < k) {
+      double v = accd[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[wid][i] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double v = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[q][threadIdx.x];
+    out[threadIdx.x] = v;
+  }
+  __syncthreads();
+}
+
+// V_i . w over [v0, v1) for i < k <= KB (rows past k predicated off), two values per
+// thread and iteration so that 2 KB loads are in flight.
+template <int KB>
+__device__ __forceinline__ void dot_rows(const SlotBuf& b, size_t v0, size_t v1, int j, int k,
+                                         double (*red)[kEngRows], double* out) {
+  const float* w = b.V + (size_t)(j + 1) * b.L;
+  float acc[KB];
+#pragma unroll
+  for (int i = 0; i < KB; ++i) acc[i] = 0.f;
+  const size_t step = (size_t)2 * blockDim.x;
+  size_t v = v0 + threadIdx.x;
+  for (; v + blockDim.x < v1; v += step) {
+    const float w0 = w[v], w1 = w[v + blockDim.x];
+#pragma unroll
+    for (int i = 0; i < KB; ++i)
+      if (i < k) {
+        const float* Vi = b.V + (size_t)i * b.L;
+        acc[i] = fmaf(Vi[v + blockDim.x], w1, fmaf(Vi[v], w0, acc[i]));
+      }
+  }
+  if (v < v1) {
+    const float w0 = w[v];
+#pragma unroll
+    for (int i = 0; i < KB; ++i)
+      if (i < k) acc[i] = fmaf(b.V[(size_t)i * b.L + v], w0, acc[i]);
+  }
+  double accd[KB];
+#pragma unroll
+  for (int i = 0; i < KB; ++i) accd[i] = (double)acc[i];
+  block_reduce_store<KB>(accd, k, red, out);
+}
+
 // partials[item][i], i < k: |R|^2 over the chunk (kPhResid) or V_i . w with
 // w = V_{j+1} (kPhArnoldi, kPhReorth; k = j + 2, per-thread sums in FP32 as in
 // the single-slab mixed path, cross-thread sums in FP64 in a fixed order).
 __global__ void __launch_bounds__(kEngThreads) eng_dot_kernel(const __grid_constant__ EngLaunch L) {
   __shared__ double red[kEngThreads / 32][kEngRows];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int n = *L.n_chunk_items;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const EngItem item = L.chunk_items[it];
@@ -38,45 +92,25 @@ __global__ void __launch_bounds__(kEngThreads) eng_dot_kernel(const __grid_const
     chunk_range(b, item.idx, &e0, &e1);
     const size_t blockvals = (size_t)b.s * b.nd * b.r;
     const size_t v0 = (size_t)e0 * blockvals, v1 = (size_t)e1 * blockvals;
-    int k;
-    double accd[kEngRows];
+    double* out = L.partials + (size_t)it * kEngRows;
     if (ph == kPhResid) {
-      k = 1;
-      double a = 0.0;
-      for (size_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) a = fma(b.R[v], b.R[v], a);
-      accd[0] = a;
+      double a[1] = {0.0};
+      for (size_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) a[0] = fma(b.R[v], b.R[v], a[0]);
+      block_reduce_store<1>(a, 1, red, out);
     } else {
       const int j = L.ctl[item.slot].j;
-      k = j + 2;
-      const float* w = b.V + (size_t)(j + 1) * b.L;
-      float acc[kEngRows];
-#pragma unroll
-      for (int i = 0; i < kEngRows; ++i) acc[i] = 0.f;
-      for (size_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-        const float wv = w[v];
-#pragma unroll
-        for (int i = 0; i < kEngRows; ++i)
-          if (i < k) acc[i] = fmaf(b.V[(size_t)i * b.L + v], wv, acc[i]);
-      }
-#pragma unroll
-      for (int i = 0; i < kEngRows; ++i) accd[i] = (double)acc[i];
-    }
-#pragma unroll
-    for (int i = 0; i < kEngRows; ++i) {
-      if (i < k) {
-        double v = accd[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[wid][i] = v;
+      const int k = j + 2;
+      switch ((k + 3) >> 2) {
+        case 1: dot_rows<4>(b, v0, v1, j, k, red, out); break;
+        case 2: dot_rows<8>(b, v0, v1, j, k, red, out); break;
+        case 3: dot_rows<12>(b, v0, v1, j, k, red, out); break;
+        case 4: dot_rows<16>(b, v0, v1, j, k, red, out); break;
+        case 5: dot_rows<20>(b, v0, v1, j, k, red, out); break;
+        case 6: dot_rows<24>(b, v0, v1, j, k, red, out); break;
+        case 7: dot_rows<28>(b, v0, v1, j, k, red, out); break;
+        default: dot_rows<32>(b, v0, v1, j, k, red, out); break;
       }
     }
-    __syncthreads();
-    if (threadIdx.x < k) {
-      double v = 0.0;
-      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[q][threadIdx.x];
-      L.partials[(size_t)it * kEngRows + threadIdx.x] = v;
-    }
-    __syncthreads();
   }
 }
 
@@ -227,6 +261,21 @@ __global__ void __launch_bounds__(kEngThreads) eng_control_kernel(const __grid_c
   }
 }
 
+// sum_{i<k} c_i X[i * ld] with four independent partial sums (loads of four rows in
+// flight), combined as (s0 + s1) + (s2 + s3).
+__device__ __forceinline__ float rows_sum(const float* c, const float* X, size_t ld, int k) {
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int i = 0;
+  for (; i + 4 <= k; i += 4) {
+    s0 = fmaf(c[i], X[(size_t)i * ld], s0);
+    s1 = fmaf(c[i + 1], X[(size_t)(i + 1) * ld], s1);
+    s2 = fmaf(c[i + 2], X[(size_t)(i + 2) * ld], s2);
+    s3 = fmaf(c[i + 3], X[(size_t)(i + 3) * ld], s3);
+  }
+  for (; i < k; ++i) s0 = fmaf(c[i], X[(size_t)i * ld], s0);
+  return (s0 + s1) + (s2 + s3);
+}
+
 // Vector update of one tick.  Thread per (element, value q of a temporal
 // node's block) of the chunk; the s temporal values of q are handled together
 // so that z = (P^-1 (x) I_r) x is formed in registers.
@@ -270,8 +319,7 @@ __global__ void __launch_bounds__(kEngThreads) eng_update_kernel(const __grid_co
         float* w = b.V + (size_t)row * b.L;
         for (int m = 0; m < s; ++m) {
           const size_t o = base + (size_t)m * tnode;
-          float acc = w[o];
-          for (int i = 0; i < k; ++i) acc = fmaf(-cf[i], b.V[(size_t)i * b.L + o], acc);
+          const float acc = w[o] - rows_sum(cf, b.V + o, b.L, k);
           w[o] = acc;
           x[m] = zs * acc;
         }
@@ -280,8 +328,7 @@ __global__ void __launch_bounds__(kEngThreads) eng_update_kernel(const __grid_co
       } else if (mode == kUpdSolve) {
         for (int m = 0; m < s; ++m) {
           const size_t o = base + (size_t)m * tnode;
-          float acc = 0.f;
-          for (int i = 0; i < k; ++i) acc = fmaf(cf[i], b.Z[(size_t)i * b.L + o], acc);
+          const float acc = rows_sum(cf, b.Z + o, b.L, k);
           const double u = b.U[o] + (double)acc;
           b.U[o] = u;
           b.U32[o] = (float)u;

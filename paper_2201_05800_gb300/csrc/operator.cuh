@@ -71,6 +71,7 @@ __host__ __device__ inline size_t op_smem_bytes(int n, int s, int epb) {
     b += (size_t)epb * DIM * ndp * vbytes;                          // gradients
     b += (size_t)epb * DIM * 2 * (nd / n) * vbytes;                 // face jumps
   }
+  b += (size_t)epb * DIM * 2 * sizeof(int);                         // neighbour elements
   return b;
 }
 
@@ -104,12 +105,30 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
   T* sC = sD + 3 * kMaxN * kMaxN;                                      // [kMaxS][kMaxS]  C
   V* sq = reinterpret_cast<V*>(sC + kMaxS * kMaxS);                    // [epb][DIM][ndp] gradients (R == 1)
   V* sjm = sq + (size_t)epb * DIM * ndp;                               // [epb][DIM][2][nf] face jumps (R == 1)
+  int* snb = reinterpret_cast<int*>(R == 1 ? sjm + (size_t)epb * DIM * 2 * nf : sq);  // [epb][DIM][2]
   const bool visc = (R == 1) && k.nu != T(0);
+  // index helpers: divisions by n, n^2, n^d are by constants (FIXED) or by multiply-high
+  auto div_n = [&](int t) { return FIXED ? t / NPX : fast_div(t, k.mg_n); };
+  auto div_n2 = [&](int t) { return FIXED ? t / (NPX * NPX) : fast_div(t, k.mg_n2); };
+  auto div_nd = [&](int t) { return FIXED ? t / ipow_c(NPX, DIM) : fast_div(t, k.mg_nd); };
+  auto div_nf = [&](int t) { return DIM == 1 ? t : (DIM == 2 ? div_n(t) : div_n2(t)); };
+  auto div_stride = [&](int t, int a) { return a == 0 ? t : (a == 1 ? div_n(t) : div_n2(t)); };
   for (int i = tid; i < 3 * kMaxN * kMaxN; i += nth) {
     const int a = i / (kMaxN * kMaxN), q = i % (kMaxN * kMaxN);
     sD[i] = k.ginv[a] * k.D[q / kMaxN][q % kMaxN];
   }
   for (int i = tid; i < kMaxS * kMaxS; i += nth) sC[i] = k.C[i / kMaxS][i % kMaxS];
+  // periodic neighbour elements of the tile, [el][a][side] (side 1: +e_a), 32-bit arithmetic
+  for (int i = tid; i < nel * DIM * 2; i += nth) {
+    const int side = i & 1, a = (i >> 1) % DIM, el = (i >> 1) / DIM;
+    const unsigned e = (unsigned)(e0 + el);
+    const unsigned K0 = (unsigned)k.K[0], K1 = (unsigned)k.K[1];
+    int ec[3] = {(int)(e % K0), (int)((e / K0) % K1), (int)(e / (K0 * K1))};
+    ec[a] += side ? 1 : -1;
+    if (ec[a] < 0) ec[a] += k.K[a];
+    if (ec[a] >= k.K[a]) ec[a] -= k.K[a];
+    snb[i] = (ec[2] * k.K[1] + ec[1]) * k.K[0] + ec[0];
+  }
 
   const size_t tnode = (size_t)nd * R;  // values of one element at one temporal node
   const int strides[3] = {1, n, n * n};
@@ -118,26 +137,27 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
 
   for (int m = 0; m < s; ++m) {
     // ---- 0. stage node m of the CTA's elements (coalesced global reads)
-    for (int idx = tid; idx < nel * (int)tnode; idx += nth) {
-      const int c = idx % R;
-      const int r2 = idx / R;
-      const int node = r2 % nd;
-      const int el = r2 / nd;
-      const size_t g = ((size_t)(e0 + el) * s + m) * tnode + (size_t)node * R + c;
-      const size_t so = ((size_t)el * R + c) * ndp + node;
-      if constexpr (MODE == kModeJvFD) {
-        su[so] = k.U[g] + k.eps * (k.vscale * k.v[g]);
-      } else if constexpr (MODE == kModeJvExact) {
-        su[so] = k.U[g];
-        sv[so] = k.vscale * k.v[g];
-      } else {
-        su[so] = k.U[g];
+    for (int t = tid; t < nel * nd; t += nth) {
+      const int el = div_nd(t), node = t - el * nd;
+      const size_t g0 = ((size_t)(e0 + el) * s + m) * tnode + (size_t)node * R;
+      const size_t so0 = ((size_t)el * R) * ndp + node;
+#pragma unroll
+      for (int c = 0; c < R; ++c) {
+        const size_t g = g0 + c, so = so0 + (size_t)c * ndp;
+        if constexpr (MODE == kModeJvFD) {
+          su[so] = k.U[g] + k.eps * (k.vscale * k.v[g]);
+        } else if constexpr (MODE == kModeJvExact) {
+          su[so] = k.U[g];
+          sv[so] = k.vscale * k.v[g];
+        } else {
+          su[so] = k.U[g];
+        }
       }
     }
     __syncthreads();
     // ---- 1. fluxes and wave speeds at every node
     for (int t = tid; t < nel * nd; t += nth) {
-      const int el = t / nd, node = t - el * nd;
+      const int el = div_nd(t), node = t - el * nd;
       const size_t so = ((size_t)el * R) * ndp + node;
       V u[R];
 #pragma unroll
@@ -157,7 +177,8 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
       if constexpr (R == 1) {
         if (visc) {
           // gradient along each direction: (2/h_a) sum_j D[i_a][j] u along the line
-          const int idx[3] = {node % n, (node / n) % n, node / (n * n)};
+          const int q1 = div_n(node), q2 = div_n(q1);
+          const int idx[3] = {node - q1 * n, q1 - q2 * n, q2};
 #pragma unroll
           for (int a = 0; a < DIM; ++a) {
             const int base = node - idx[a] * strides[a];
@@ -178,8 +199,9 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
     __syncthreads();
     // ---- 2. volume term
     for (int t = tid; t < nel * nd; t += nth) {
-      const int el = t / nd, node = t - el * nd;
-      const int idx[3] = {node % n, (node / n) % n, node / (n * n)};
+      const int el = div_nd(t), node = t - el * nd;
+      const int q1 = div_n(node), q2 = div_n(q1);
+      const int idx[3] = {node - q1 * n, q1 - q2 * n, q2};
       const V* sfe = sf + (size_t)el * DIM * R * ndp;
       V acc[R];
 #pragma unroll
@@ -229,21 +251,16 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
       for (int t = tid; t < 2 * nel * nf; t += nth) {
         const int side = t < nel * nf ? 1 : 0;  // 1: upper face (normal +e_a), 0: lower face
         const int tt = side ? t : t - nel * nf;
-        const int el = tt / nf;
+        const int el = div_nf(tt);
         const int fidx = tt - el * nf;
         // own node: insert i_a into the face index
-        const int lo = fidx % strides[a];
-        const int hi = fidx / strides[a];
+        const int hi = div_stride(fidx, a);
+        const int lo = fidx - hi * strides[a];
         const int ia_own = side ? n - 1 : 0;
         const int own = lo + ia_own * strides[a] + hi * strides[a] * n;
         const int nbr_node = lo + (n - 1 - ia_own) * strides[a] + hi * strides[a] * n;
-        // neighbour element (periodic)
-        const long long e = e0 + el;
-        long long ec[3] = {e % k.K[0], (e / k.K[0]) % k.K[1], e / ((long long)k.K[0] * k.K[1])};
-        ec[a] += side ? 1 : -1;
-        if (ec[a] < 0) ec[a] += k.K[a];
-        if (ec[a] >= k.K[a]) ec[a] -= k.K[a];
-        const long long en = (ec[2] * k.K[1] + ec[1]) * k.K[0] + ec[0];
+        // neighbour element (periodic), from the tile's table
+        const long long en = snb[(el * DIM + a) * 2 + side];
         const long long eln = en - e0;
         const bool internal = eln >= 0 && eln < nel;
         if (!side && internal) continue;  // computed by the neighbour's upper item
@@ -344,14 +361,16 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
         // ---- 3b. lift of the face jumps along the normal lines (symmetry term of the
         //          SIPG form): F_I += nu/2 (2/h_a)^2 (1/w_i) (D[N][i] [[u]]_up + D[0][i] [[u]]_lo)
         for (int t = tid; t < nel * nd; t += nth) {
-          const int el = t / nd, node = t - el * nd;
-          const int idx[3] = {node % n, (node / n) % n, node / (n * n)};
+          const int el = div_nd(t), node = t - el * nd;
+          const int q1 = div_n(node), q2 = div_n(q1);
+          const int idx[3] = {node - q1 * n, q1 - q2 * n, q2};
           V acc = sr[(size_t)el * ndp + node];
 #pragma unroll
           for (int a = 0; a < DIM; ++a) {
             const int ia = idx[a];
-            const int lo = node % strides[a];
-            const int hi = node / (strides[a] * n);
+            // face index: node with digit a removed
+            const int lo = a == 0 ? 0 : (a == 1 ? idx[0] : idx[0] + idx[1] * n);
+            const int hi = a == 0 ? idx[1] + idx[2] * n : (a == 1 ? idx[2] : 0);
             const int fidx = lo + hi * strides[a];
             const V* sja = sjm + ((size_t)el * DIM + a) * 2 * nf;
             acc = acc + k.vup[a][ia] * sja[nf + fidx] + k.vlo[a][ia] * sja[fidx];
@@ -378,8 +397,8 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
       for (int t = tid; t < nel * (int)tnode; t += nth) {
         const int c = t % R;
         const int r2 = t / R;
-        const int node = r2 % nd;
-        const int el = r2 / nd;
+        const int el = div_nd(r2);
+        const int node = r2 - el * nd;
         const size_t gb = (size_t)(e0 + el) * s * tnode + (size_t)node * R + c;  // (e, j = 0, node, c)
         const size_t g = gb + (size_t)m * tnode;
         const V Fv = sr[((size_t)el * R + c) * ndp + node];

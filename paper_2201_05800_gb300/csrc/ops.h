@@ -33,6 +33,7 @@ inline size_t operator_smem_bytes(int dim, int r, size_t tsize, int mode, int n,
     b += (size_t)epb * dim * ndp * vbytes;
     b += (size_t)epb * dim * 2 * (nd / n) * vbytes;
   }
+  b += (size_t)epb * dim * 2 * sizeof(int);  // neighbour elements of the tile
   return b;
 }
 
