@@ -44,36 +44,52 @@ __device__ __forceinline__ void block_reduce_store(const double (&accd)[KB], int
   __syncthreads();
 }
 
-// V_i . w over [v0, v1) for i < k <= KB (rows past k predicated off), two values per
-// thread and iteration so that 2 KB loads are in flight.
-template <int KB>
+// V_i . w over [v0, v1) for i < k, in passes over groups of 8 rows (few registers, so many
+// blocks stay resident; w is re-read from L1/L2 once per group), two values per thread and
+// iteration.  Per-warp sums of each row go to red[warp][row]; then one fixed-order sum.
 __device__ __forceinline__ void dot_rows(const SlotBuf& b, size_t v0, size_t v1, int j, int k,
                                          double (*red)[kEngRows], double* out) {
+  constexpr int G = 8;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const float* w = b.V + (size_t)(j + 1) * b.L;
-  float acc[KB];
+  for (int g0 = 0; g0 < k; g0 += G) {
+    float acc[G];
 #pragma unroll
-  for (int i = 0; i < KB; ++i) acc[i] = 0.f;
-  const size_t step = (size_t)2 * blockDim.x;
-  size_t v = v0 + threadIdx.x;
-  for (; v + blockDim.x < v1; v += step) {
-    const float w0 = w[v], w1 = w[v + blockDim.x];
+    for (int i = 0; i < G; ++i) acc[i] = 0.f;
+    const size_t step = (size_t)2 * blockDim.x;
+    size_t v = v0 + threadIdx.x;
+    for (; v + blockDim.x < v1; v += step) {
+      const float w0 = w[v], w1 = w[v + blockDim.x];
 #pragma unroll
-    for (int i = 0; i < KB; ++i)
-      if (i < k) {
-        const float* Vi = b.V + (size_t)i * b.L;
-        acc[i] = fmaf(Vi[v + blockDim.x], w1, fmaf(Vi[v], w0, acc[i]));
+      for (int i = 0; i < G; ++i)
+        if (g0 + i < k) {
+          const float* Vi = b.V + (size_t)(g0 + i) * b.L;
+          acc[i] = fmaf(Vi[v + blockDim.x], w1, fmaf(Vi[v], w0, acc[i]));
+        }
+    }
+    if (v < v1) {
+      const float w0 = w[v];
+#pragma unroll
+      for (int i = 0; i < G; ++i)
+        if (g0 + i < k) acc[i] = fmaf(b.V[(size_t)(g0 + i) * b.L + v], w0, acc[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      if (g0 + i < k) {
+        double d = (double)acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+        if (lane == 0) red[wid][g0 + i] = d;
       }
+    }
   }
-  if (v < v1) {
-    const float w0 = w[v];
-#pragma unroll
-    for (int i = 0; i < KB; ++i)
-      if (i < k) acc[i] = fmaf(b.V[(size_t)i * b.L + v], w0, acc[i]);
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double d = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) d += red[q][threadIdx.x];
+    out[threadIdx.x] = d;
   }
-  double accd[KB];
-#pragma unroll
-  for (int i = 0; i < KB; ++i) accd[i] = (double)acc[i];
-  block_reduce_store<KB>(accd, k, red, out);
+  __syncthreads();
 }
 
 // partials[item][i], i < k: |R|^2 over the chunk (kPhResid) or V_i . w with
@@ -99,17 +115,7 @@ __global__ void __launch_bounds__(kEngThreads) eng_dot_kernel(const __grid_const
       block_reduce_store<1>(a, 1, red, out);
     } else {
       const int j = L.ctl[item.slot].j;
-      const int k = j + 2;
-      switch ((k + 3) >> 2) {
-        case 1: dot_rows<4>(b, v0, v1, j, k, red, out); break;
-        case 2: dot_rows<8>(b, v0, v1, j, k, red, out); break;
-        case 3: dot_rows<12>(b, v0, v1, j, k, red, out); break;
-        case 4: dot_rows<16>(b, v0, v1, j, k, red, out); break;
-        case 5: dot_rows<20>(b, v0, v1, j, k, red, out); break;
-        case 6: dot_rows<24>(b, v0, v1, j, k, red, out); break;
-        case 7: dot_rows<28>(b, v0, v1, j, k, red, out); break;
-        default: dot_rows<32>(b, v0, v1, j, k, red, out); break;
-      }
+      dot_rows(b, v0, v1, j, j + 2, red, out);
     }
   }
 }
@@ -266,6 +272,15 @@ __global__ void __launch_bounds__(kEngThreads) eng_control_kernel(const __grid_c
 __device__ __forceinline__ float rows_sum(const float* c, const float* X, size_t ld, int k) {
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
   int i = 0;
+  for (; i + 8 <= k; i += 8) {  // eight rows in flight
+    const float x0 = X[(size_t)i * ld], x1 = X[(size_t)(i + 1) * ld], x2 = X[(size_t)(i + 2) * ld],
+                x3 = X[(size_t)(i + 3) * ld], x4 = X[(size_t)(i + 4) * ld], x5 = X[(size_t)(i + 5) * ld],
+                x6 = X[(size_t)(i + 6) * ld], x7 = X[(size_t)(i + 7) * ld];
+    s0 = fmaf(c[i + 4], x4, fmaf(c[i], x0, s0));
+    s1 = fmaf(c[i + 5], x5, fmaf(c[i + 1], x1, s1));
+    s2 = fmaf(c[i + 6], x6, fmaf(c[i + 2], x2, s2));
+    s3 = fmaf(c[i + 7], x7, fmaf(c[i + 3], x3, s3));
+  }
   for (; i + 4 <= k; i += 4) {
     s0 = fmaf(c[i], X[(size_t)i * ld], s0);
     s1 = fmaf(c[i + 1], X[(size_t)(i + 1) * ld], s1);
@@ -360,7 +375,9 @@ __global__ void __launch_bounds__(kEngThreads) eng_update_kernel(const __grid_co
 // The elements of a chunk are processed in groups held in shared memory.
 __global__ void __launch_bounds__(kEngThreads) eng_kron_kernel(const __grid_constant__ EngLaunch L) {
   constexpr int kBuf = 2048;  // floats per ping-pong buffer
+  constexpr int kKd = 4 * kMaxN * kMaxN + kMaxN * kMaxN * kMaxS * kMaxS;  // 2D data of the largest class
   __shared__ float sa[kBuf], sb2[kBuf];
+  __shared__ float skd[kKd];
   const int nitems = *L.n_chunk_items;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const EngItem item = L.chunk_items[it];
@@ -376,7 +393,10 @@ __global__ void __launch_bounds__(kEngThreads) eng_kron_kernel(const __grid_cons
     const int n = b.n, s = b.s, nd = b.nd, dim = b.dim;
     const int per = s * nd;  // values of one element (r = 1)
     const int E = kBuf / per > 0 ? kBuf / per : 1;
-    const float* Vxi = b.kdat;
+    const int nkd = 4 * n * n + nd * s * s;
+    for (int i = threadIdx.x; i < nkd; i += blockDim.x) skd[i] = b.kdat[i];
+    __syncthreads();
+    const float* Vxi = skd;
     const float* Vx = Vxi + n * n;
     const float* Vyi = Vx + n * n;
     const float* Vy = Vyi + n * n;
