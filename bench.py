@@ -357,6 +357,7 @@ def gpu_arm(args):
             if "batched" in args.legs and ws == 1 else None
         served = _serving_leg(stdg, [int(r) for r in args.serve_rates.split(",")], args.serve_requests) \
             if "serving" in args.legs and ws == 1 else None
+        wave3d = _density_wave_leg(stdg, stream) if "wave3d" in args.legs and ws == 1 else None
 
     lat_ms = sorted(1e3 * x for x in lat)
     cpu = None
@@ -392,7 +393,7 @@ def gpu_arm(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hin.numel() * 8),
                         "d2h_bytes_per_step": int(hout.numel() * 8)},
                 "gpu_launches": launches, "cpu_baseline": cpu, "mixed_fp32": mixed,
-                "batched": batched, "served": served}
+                "batched": batched, "served": served, "density_wave_3d": wave3d}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -643,6 +644,59 @@ def _serving_leg(stdg, rates, n_req):
     return out
 
 
+def _density_wave_leg(stdg, stream, slabs=2):
+    """3D Euler density wave (rho = 1 + 0.2 sin(2 pi (x+y+z)), v = (1,1,1), p = 1) on the periodic
+    unit cube, 32^3 hexes, N = 3, s = 3 (31.5 M space-time DOF), CFL 0.5: one warm-up slab and
+    `slabs` timed slabs on the FP64 path (FD Jv) and on the mixed path (FP32 exact Jv and Krylov
+    basis, FP64 Newton refinement); differences between the paths and to the exact solution."""
+    import ctypes
+    import numpy as np
+    import torch
+    from paper_2201_05800_gb300 import inputs
+    K, N, s = 32, 3, 3
+    base = dict(dim=3, cells=[K, K, K], lo=[0, 0, 0], hi=[1, 1, 1], N=N, s=s, equation=stdg.EULER, gamma=1.4,
+                dt=1.0, newton_rtol=1e-10, gmres_m=30, gmres_rtol=1e-3, newton_maxit=30, gmres_maxit=600)
+    d = stdg.make_config(**base)
+    with stdg.Context(d, stream.cuda_stream) as c:
+        X = c.node_coordinates()
+    u0 = np.ascontiguousarray(inputs.density_wave(X[:, 0], X[:, 1], X[:, 2]).ravel())
+    ur = u0.reshape(-1, 5)
+    rho = ur[:, 0]
+    p = 0.4 * (ur[:, 4] - 0.5 * (ur[:, 1] ** 2 + ur[:, 2] ** 2 + ur[:, 3] ** 2) / rho)
+    lam = float(np.max(np.abs(ur[:, 1] / rho) + np.sqrt(1.4 * p / rho)))
+    dt = 0.5 * (1.0 / K) / lam
+    out = {"workload": "3D Euler density wave on the periodic unit cube, 32^3 hexes, N=3, s=3, CFL 0.5 "
+                       "(dt = %.6g), Newton rtol 1e-10, GMRES(30) rtol 1e-3" % dt}
+    finals = {}
+    for name, prec, jv in (("fp64", stdg.FP64, stdg.JV_FD), ("mixed_fp32", stdg.MIXED_FP32, stdg.JV_EXACT)):
+        dd = stdg.make_config(**dict(base, dt=dt, precision=prec, jv_mode=jv))
+        with stdg.Context(dd, stream.cuda_stream) as c:
+            dof = c.slab_len
+            c.set_state(u0)
+            c.advance_slab()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            st = [c.advance_slab() for _ in range(slabs)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            finals[name] = c.get_state()
+            evals = sum(x["residual_evals"] + x["jv_evals"] for x in st)
+            out[name] = {"ms_per_slab": ms / slabs, "gdof_evals_per_s": evals * dof / (ms * 1e-3) / 1e9,
+                         "newton_its": [x["newton_its"] for x in st], "gmres_its": [x["gmres_its"] for x in st],
+                         "device_gb": c.device_bytes / 1e9}
+    t = (slabs + 1) * dt
+    exact = inputs.density_wave(X[:, 0], X[:, 1], X[:, 2], t=t).ravel()
+    for name in finals:
+        out[name]["rel_l2_nodal_vs_exact"] = float(np.linalg.norm(finals[name] - exact) / np.linalg.norm(exact))
+    out["dof_st"] = int(dof)
+    out["rel_l2_mixed_vs_fp64"] = float(np.linalg.norm(finals["mixed_fp32"] - finals["fp64"]) /
+                                        np.linalg.norm(finals["fp64"]))
+    out["speedup_mixed"] = out["fp64"]["ms_per_slab"] / out["mixed_fp32"]["ms_per_slab"]
+    return out
+
+
 def _ncu_traffic():
     """DRAM bytes per launch of the FD Jv kernel from the committed ncu summary, or None."""
     p = os.path.join(ROOT, "profiles", "jv_fd_euler2d_vortex64.txt")
@@ -664,8 +718,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="mixed,batched,serving",
-                    help="extra legs after the main FP64 line: mixed,batched,serving")
+    ap.add_argument("--legs", default="mixed,batched,serving,wave3d",
+                    help="extra legs after the main FP64 line: mixed,batched,serving,wave3d (or none)")
     ap.add_argument("--batch-instances", type=int, default=4096)
     ap.add_argument("--batch-sequential", type=int, default=48,
                     help="instances solved one at a time for the batched-vs-sequential comparison")

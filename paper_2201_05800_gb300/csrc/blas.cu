@@ -148,9 +148,33 @@ unsigned grid_for(size_t L) {
   return (unsigned)b;
 }
 
+// Blocks of the dot pass: one wave (the resident blocks of this row count on every SM), at
+// most the partials buffer's nblk rows; cached per instantiation.
 template <class TV, class TW, int K>
-cudaError_t multidot_k(const TV* V, size_t ld, const TW* w, size_t L, double* partials, int nblk, cudaStream_t st) {
-  multidot_kernel<TV, TW, K><<<nblk, kRedThreads, 0, st>>>(V, ld, w, L, partials);
+int multidot_grid(int nblk) {
+  static int per_sm = 0;
+  static int sms = 0;
+  if (per_sm == 0) {
+    int dev = 0, occ = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, multidot_kernel<TV, TW, K>, kRedThreads, 0) !=
+            cudaSuccess ||
+        occ < 1)
+      occ = 1;
+    sms = n > 0 ? n : 1;
+    per_sm = occ;
+  }
+  const int g = per_sm * sms;
+  return g < nblk ? g : nblk;
+}
+
+template <class TV, class TW, int K>
+cudaError_t multidot_k(const TV* V, size_t ld, const TW* w, size_t L, double* partials, int nblk, cudaStream_t st,
+                       int* used) {
+  const int g = multidot_grid<TV, TW, K>(nblk);
+  multidot_kernel<TV, TW, K><<<g, kRedThreads, 0, st>>>(V, ld, w, L, partials);
+  if (used) *used = g;
   return cudaGetLastError();
 }
 
@@ -158,9 +182,9 @@ cudaError_t multidot_k(const TV* V, size_t ld, const TW* w, size_t L, double* pa
 
 template <class TV, class TW>
 cudaError_t multidot(const TV* V, size_t ld, int k, const TW* w, size_t L, double* partials, int nblk,
-                     cudaStream_t st) {
+                     cudaStream_t st, int* used) {
 #define STDG_DOT_CASE(K) \
-  case K: return multidot_k<TV, TW, K>(V, ld, w, L, partials, nblk, st);
+  case K: return multidot_k<TV, TW, K>(V, ld, w, L, partials, nblk, st, used);
   switch (k) {
     STDG_DOT_CASE(1) STDG_DOT_CASE(2) STDG_DOT_CASE(3) STDG_DOT_CASE(4) STDG_DOT_CASE(5) STDG_DOT_CASE(6)
     STDG_DOT_CASE(7) STDG_DOT_CASE(8) STDG_DOT_CASE(9) STDG_DOT_CASE(10) STDG_DOT_CASE(11) STDG_DOT_CASE(12)
@@ -211,8 +235,10 @@ cudaError_t extract_last(T* u, const T* U, long long nelem, int s, int blk, cuda
   return cudaGetLastError();
 }
 
-template cudaError_t multidot<double, double>(const double*, size_t, int, const double*, size_t, double*, int, cudaStream_t);
-template cudaError_t multidot<float, float>(const float*, size_t, int, const float*, size_t, double*, int, cudaStream_t);
+template cudaError_t multidot<double, double>(const double*, size_t, int, const double*, size_t, double*, int, cudaStream_t,
+                                              int*);
+template cudaError_t multidot<float, float>(const float*, size_t, int, const float*, size_t, double*, int, cudaStream_t,
+                                            int*);
 template cudaError_t update<double, double>(double*, const double*, size_t, int, const Coefs&, size_t, cudaStream_t);
 template cudaError_t update<float, float>(float*, const float*, size_t, int, const Coefs&, size_t, cudaStream_t);
 template cudaError_t update<float, double>(double*, const float*, size_t, int, const Coefs&, size_t, cudaStream_t);

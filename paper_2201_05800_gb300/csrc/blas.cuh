@@ -25,10 +25,11 @@ struct Coefs {
   double c[kMaxDots];
 };
 
-// partials[b*kPartialStride + i] = sum over block b of V_i . w   (i < k <= kMaxDots)
+// partials[b*kPartialStride + i] = sum over block b of V_i . w   (i < k <= kMaxDots), for the
+// blocks b < *used (at most nblk: one wave of the resident blocks of this row count).
 template <class TV, class TW>
 cudaError_t multidot(const TV* V, size_t ld, int k, const TW* w, size_t L, double* partials, int nblk,
-                     cudaStream_t st);
+                     cudaStream_t st, int* used);
 
 // w -= sum_{i<k} c.c[i] V_i   (k <= kMaxDots)
 template <class TV, class TW>

@@ -319,8 +319,9 @@ stdg_status op_jv(stdg_ctx* c, const double* U, const double* F0, const double* 
 // ---- reductions
 template <class T>
 stdg_status dots_to_small(stdg_ctx* c, const T* V, int k, const T* w, int small_off) {
-  PK(c, 2, (multidot<T, T>(V, c->slab_len, k, w, c->slab_len, c->partials, c->nblk, c->st)));
-  PK(c, 2, reduce_partials(c->partials, c->nblk, k, c->small + small_off, c->st));
+  int used = c->nblk;
+  PK(c, 2, (multidot<T, T>(V, c->slab_len, k, w, c->slab_len, c->partials, c->nblk, c->st, &used)));
+  PK(c, 2, reduce_partials(c->partials, used, k, c->small + small_off, c->st));
   return STDG_OK;
 }
 
@@ -332,8 +333,9 @@ stdg_status fetch_small(stdg_ctx* c, int off, int count) {
 
 template <class T>
 stdg_status norm2(stdg_ctx* c, const T* x, size_t L, double* out) {
-  PK(c, 2, (multidot<T, T>(x, L, 1, x, L, c->partials, c->nblk, c->st)));
-  PK(c, 2, reduce_partials(c->partials, c->nblk, 1, c->small + 200, c->st));
+  int used = c->nblk;
+  PK(c, 2, (multidot<T, T>(x, L, 1, x, L, c->partials, c->nblk, c->st, &used)));
+  PK(c, 2, reduce_partials(c->partials, used, 1, c->small + 200, c->st));
   CKS(fetch_small(c, 200, 1));
   *out = std::sqrt(c->hpin[200]);
   return STDG_OK;

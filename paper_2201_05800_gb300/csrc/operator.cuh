@@ -131,6 +131,7 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
   }
 
   const size_t tnode = (size_t)nd * R;  // values of one element at one temporal node
+  const T ev = k.eps * k.vscale;         // FD Jv: U + (eps vscale) v, one FMA per value
   const int strides[3] = {1, n, n * n};
   // the tile the temporal coupling acts on: U for the residual, v for J v
   const T* gtile = (MODE == kModeResidual) ? k.U : k.v;
@@ -145,7 +146,7 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
       for (int c = 0; c < R; ++c) {
         const size_t g = g0 + c, so = so0 + (size_t)c * ndp;
         if constexpr (MODE == kModeJvFD) {
-          su[so] = k.U[g] + k.eps * (k.vscale * k.v[g]);
+          su[so] = fma(ev, k.v[g], k.U[g]);
         } else if constexpr (MODE == kModeJvExact) {
           su[so] = k.U[g];
           sv[so] = k.vscale * k.v[g];
@@ -248,6 +249,7 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const T g = k.ginv[a] * k.winv_end;
+      const T gh = T(0.5) * g;
       for (int t = tid; t < 2 * nel * nf; t += nth) {
         const int side = t < nel * nf ? 1 : 0;  // 1: upper face (normal +e_a), 0: lower face
         const int tt = side ? t : t - nel * nf;
@@ -289,9 +291,11 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
         } else {
           const size_t gofs = ((size_t)en * s + m) * tnode + (size_t)nbr_node * R;
 #pragma unroll
-          for (int c = 0; c < R; ++c)
-            up[c] = eval_state<MODE>(k.U[gofs + c], MODE == kModeResidual ? T(0) : k.vscale * k.v[gofs + c],
-                                     k.eps);
+          for (int c = 0; c < R; ++c) {
+            if constexpr (MODE == kModeJvFD) up[c] = fma(ev, k.v[gofs + c], k.U[gofs + c]);
+            else up[c] = eval_state<MODE>(k.U[gofs + c], MODE == kModeResidual ? T(0) : k.vscale * k.v[gofs + c],
+                                          k.eps);
+          }
           lp = P::flux_speed(up, a, fp, k);
           if constexpr (R == 1) {
             if (visc) {
@@ -303,8 +307,10 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
               for (int j = 0; j < NPX; ++j) {
                 if (FIXED || j < n) {
                   const size_t gj = lbase + (size_t)j * strides[a] * R;
-                  qp = qp + Db[j] * eval_state<MODE>(k.U[gj], MODE == kModeResidual ? T(0) : k.vscale * k.v[gj],
-                                                     k.eps);
+                  if constexpr (MODE == kModeJvFD) qp = qp + Db[j] * fma(ev, k.v[gj], k.U[gj]);
+                  else
+                    qp = qp + Db[j] * eval_state<MODE>(k.U[gj], MODE == kModeResidual ? T(0) : k.vscale * k.v[gj],
+                                                       k.eps);
                 }
               }
             }
@@ -316,11 +322,13 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
         if (side) {  // own element below the face: uL = u-, uR = u+
           const V lam = dmax(lm, lp);
           V* srn = sr + (size_t)(internal ? eln : el) * R * ndp;
+          // with H = (fm + fp)/2 - lam (up - um)/2:  H - fm = (df - lam du)/2 and
+          // H - fp = -(df + lam du)/2, df = fp - fm, du = up - um
 #pragma unroll
           for (int c = 0; c < R; ++c) {
-            const V H = T(0.5) * (fm[c] + fp[c]) - T(0.5) * (lam * (up[c] - um[c]));
-            sre[c * ndp + own] = sre[c * ndp + own] - g * (H - fm[c]);  // n = +e_a
-            if (internal) srn[c * ndp + nbr_node] = srn[c * ndp + nbr_node] + g * (H - fp[c]);  // n = -e_a
+            const V du = up[c] - um[c], df = fp[c] - fm[c];
+            sre[c * ndp + own] = sre[c * ndp + own] - gh * (df - lam * du);  // n = +e_a
+            if (internal) srn[c * ndp + nbr_node] = srn[c * ndp + nbr_node] - gh * (df + lam * du);  // n = -e_a
           }
           if constexpr (R == 1) {
             if (visc) {
@@ -339,10 +347,12 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
           }
         } else {     // own element above the face: uL = u+, uR = u-
           const V lam = dmax(lp, lm);
+          // own element above: H = (fp + fm)/2 - lam (um - up)/2, H - fm = (df - lam du)/2
+          // with df = fp - fm, du = um - up
 #pragma unroll
           for (int c = 0; c < R; ++c) {
-            const V H = T(0.5) * (fp[c] + fm[c]) - T(0.5) * (lam * (um[c] - up[c]));
-            sre[c * ndp + own] = sre[c * ndp + own] + g * (H - fm[c]);
+            const V du = um[c] - up[c], df = fp[c] - fm[c];
+            sre[c * ndp + own] = sre[c * ndp + own] + gh * (df - lam * du);
           }
           if constexpr (R == 1) {
             if (visc) {
