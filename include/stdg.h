@@ -182,6 +182,18 @@ stdg_status stdg_spatial_operator(stdg_ctx* ctx, const double* U, double* F, int
 stdg_status stdg_jv_fd_apply(stdg_ctx* ctx, const double* U, const double* F0, const double* v, double eps,
                              double* Jv);
 
+/* The method-of-lines DG-SEM + Lobatto IIIC slab residual (the LoDG form of
+ * Sec. 5, Eq. DG_vs_RK:RK) with the Butcher matrix A = 1/2 Dtilde^-1,
+ * Dtilde = D_tau + M_tau^-1 e_1 e_1^T (Eq. SBP_to_RK), from the same F(U):
+ *   form 0:  R = U - 1 (x) u_prev - dt (A (x) I) F(U)
+ *   form 1:  R = ((dt A)^-1 (x) I)(U - 1 (x) u_prev) - F(U)   (the A^-1 form whose
+ *            Jacobian is Eq. Jacobian_Ainv)
+ * U, R: slab layout (slab_len values); u_prev: state layout.  Both vanish at
+ * the solution of stdg_residual (equivalence of the two formulations): the
+ * space-time residual equals -(dt/2)(M_tau (x) I) times the form-1 residual. */
+stdg_status stdg_lodg_residual(stdg_ctx* ctx, const double* U, const double* u_prev, double* R, int form,
+                               int ptr_kind);
+
 /* z = (P(U)^-1 (x) I_r) v with the point-block matrices P_I of
  * STDG_PRECOND_POINT_BLOCK built from the slab U (U, v, z: slab_len values).
  * For linear advection P_I (x) I_r is exactly the block of Eq. Jacobian_ST

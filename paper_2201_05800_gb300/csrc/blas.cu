@@ -120,6 +120,29 @@ __global__ void tnode_scale_add_kernel(T* y, const T* x, double a, const TimeWei
   }
 }
 
+__global__ void lodg_combine_kernel(double* __restrict__ R, const double* __restrict__ U,
+                                    const double* __restrict__ F, const double* __restrict__ u_prev,
+                                    const StageMatrix A, double dt, int form, long long nelem, int s, int blk) {
+  const size_t total = (size_t)nelem * blk;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const double idt = 1.0 / dt;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+    const size_t e = idx / blk, q = idx % blk;
+    const size_t base = e * s * blk + q;
+    const double un = u_prev[idx];
+    for (int m = 0; m < s; ++m) {
+      double acc = 0.0;
+      if (form == 0) {
+        for (int j = 0; j < s; ++j) acc = fma(A.a[m][j], F[base + (size_t)j * blk], acc);
+        R[base + (size_t)m * blk] = (U[base + (size_t)m * blk] - un) - dt * acc;
+      } else {
+        for (int j = 0; j < s; ++j) acc = fma(A.a[m][j], U[base + (size_t)j * blk] - un, acc);
+        R[base + (size_t)m * blk] = acc * idt - F[base + (size_t)m * blk];
+      }
+    }
+  }
+}
+
 template <class T>
 __global__ void broadcast_kernel(T* __restrict__ U, const T* __restrict__ u, long long nelem, int s, int blk) {
   const size_t total = (size_t)nelem * s * blk;
@@ -220,6 +243,12 @@ template <class T>
 cudaError_t tnode_scale_add(T* y, const T* x, double a, const TimeWeights& w, const T* z, double b,
                             long long nelem, int s, int blk, cudaStream_t st) {
   tnode_scale_add_kernel<T><<<grid_for((size_t)nelem * s * blk), 256, 0, st>>>(y, x, a, w, z, b, nelem, s, blk);
+  return cudaGetLastError();
+}
+
+cudaError_t lodg_combine(double* R, const double* U, const double* F, const double* u_prev, const StageMatrix& A,
+                         double dt, int form, long long nelem, int s, int blk, cudaStream_t st) {
+  lodg_combine_kernel<<<grid_for((size_t)nelem * blk), 256, 0, st>>>(R, U, F, u_prev, A, dt, form, nelem, s, blk);
   return cudaGetLastError();
 }
 

@@ -51,6 +51,15 @@ template <class T>
 cudaError_t tnode_scale_add(T* y, const T* x, double a, const TimeWeights& w, const T* z, double b,
                             long long nelem, int s, int per_node_block, cudaStream_t st);
 
+// Method-of-lines (Lobatto IIIC) stage residual from F(U), per value q of a node block:
+//   form 0:  R_m = U_m - u^n - dt sum_j A[m][j] F_j            (Eq. DG_vs_RK:RK)
+//   form 1:  R_m = sum_j Ainv[m][j] (U_j - u^n) / dt - F_m     (the A^-1 form, Eq. Jacobian_Ainv)
+struct StageMatrix {
+  double a[8][8];
+};
+cudaError_t lodg_combine(double* R, const double* U, const double* F, const double* u_prev, const StageMatrix& A,
+                         double dt, int form, long long nelem, int s, int per_node_block, cudaStream_t st);
+
 // U[e][m][:] = u[e][:] for all m (initial guess 1 (x) u^n)
 template <class T>
 cudaError_t broadcast_slab(T* U, const T* u, long long nelem, int s, int per_node_block, cudaStream_t st);

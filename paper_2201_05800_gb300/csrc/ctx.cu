@@ -822,6 +822,65 @@ stdg_status stdg_jv_fd_apply(stdg_ctx* c, const double* U, const double* F0, con
   return STDG_OK;
 }
 
+stdg_status stdg_lodg_residual(stdg_ctx* c, const double* U, const double* uprev, double* R, int form,
+                               int kind) {
+  if (!c || !U || !uprev || !R || (form != 0 && form != 1) || (kind != STDG_HOST && kind != STDG_DEVICE))
+    return STDG_ERR_INVALID_ARG;
+  DevGuard g(c->device);
+  // Lobatto IIIC matrix from the temporal DG-SEM matrices (Eq. SBP_to_RK):
+  // A = 1/2 Dtilde^-1, Dtilde = D_tau + M_tau^-1 e_1 e_1^T; the A^-1 form uses 2 Dtilde
+  const int s = c->s;
+  double tau[16], om[16], Dt[256];
+  lgl_rule(s, tau, om);
+  diff_matrix(s, tau, Dt);
+  double W[kMaxS][2 * kMaxS];
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) {
+      W[i][j] = Dt[i * s + j] + (i == 0 && j == 0 ? 1.0 / om[0] : 0.0);
+      W[i][s + j] = i == j ? 1.0 : 0.0;
+    }
+  StageMatrix A;
+  std::memset(&A, 0, sizeof(A));
+  if (form == 1) {
+    for (int i = 0; i < s; ++i)
+      for (int j = 0; j < s; ++j) A.a[i][j] = 2.0 * W[i][j];
+  } else {
+    for (int col = 0; col < s; ++col) {
+      int pv = col;
+      for (int q = col + 1; q < s; ++q)
+        if (std::fabs(W[q][col]) > std::fabs(W[pv][col])) pv = q;
+      for (int j = 0; j < 2 * s; ++j) std::swap(W[col][j], W[pv][j]);
+      const double inv = 1.0 / W[col][col];
+      for (int j = 0; j < 2 * s; ++j) W[col][j] *= inv;
+      for (int q = 0; q < s; ++q)
+        if (q != col) {
+          const double f = W[q][col];
+          for (int j = 0; j < 2 * s; ++j) W[q][j] -= f * W[col][j];
+        }
+    }
+    for (int i = 0; i < s; ++i)
+      for (int j = 0; j < s; ++j) A.a[i][j] = 0.5 * W[i][s + j];
+  }
+  const double* dU = U;
+  const double* du = uprev;
+  double* dR = R;
+  if (kind == STDG_HOST) {
+    CK(c, cudaMemcpyAsync(c->X1, U, c->slab_len * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(c, cudaMemcpyAsync(c->Xs, uprev, c->state_len * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    dU = c->X1;
+    du = c->Xs;
+    dR = c->R;
+  }
+  // F(U) at every temporal node into X2, then the stage combination
+  CKS(op_residual(c, dU, du, nullptr, c->X2));
+  PK(c, 3, lodg_combine(dR, dU, c->X2, du, A, c->d.dt, form, c->nelem, c->s, c->nd * c->r, c->st));
+  if (kind == STDG_HOST) {
+    CK(c, cudaMemcpyAsync(R, dR, c->slab_len * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+  }
+  return STDG_OK;
+}
+
 stdg_status stdg_precond_apply(stdg_ctx* c, const double* U, const double* v, double* z, int kind) {
   if (!c || !U || !v || !z || (kind != STDG_HOST && kind != STDG_DEVICE)) return STDG_ERR_INVALID_ARG;
   DevGuard g(c->device);

@@ -82,6 +82,7 @@ _SIGS = {
     "stdg_spatial_operator": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "stdg_jv_fd_apply": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, _P]),
     "stdg_precond_apply": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
+    "stdg_lodg_residual": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int]),
     "stdg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "stdg_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(stdg_profile), ctypes.c_int]),
     "stdg_last_error": (ctypes.c_char_p, [_P]),
@@ -248,6 +249,16 @@ class Context:
         if any(k != DEVICE for _, k in ptrs):
             raise TypeError("jv_fd_apply takes device tensors")
         self._check(self._lib.stdg_jv_fd_apply(self._h, ptrs[0][0], ptrs[1][0], ptrs[2][0], float(eps), ptrs[3][0]))
+        return out
+
+    def lodg_residual(self, U, u_prev, form=0, out=None):
+        """Lobatto IIIC (method-of-lines) slab residual, form 0 (A) or 1 (A^-1)."""
+        out = (np.empty(self.slab_len) if isinstance(U, np.ndarray) else U.new_empty(self.slab_len)) \
+            if out is None else out
+        ptrs = [_ptr(x, None) for x in (U, u_prev, out)]
+        if len({k for _, k in ptrs}) != 1:
+            raise TypeError("all buffers must be on the same side (host or device)")
+        self._check(self._lib.stdg_lodg_residual(self._h, ptrs[0][0], ptrs[1][0], ptrs[2][0], int(form), ptrs[0][1]))
         return out
 
     def precond_apply(self, U, v, out=None):
