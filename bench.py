@@ -297,7 +297,10 @@ def gpu_arm(args):
         cls = max(prof, key=lambda k: prof[k]["ms"])
         n, s = w["N"] + 1, w["s"]
         nodes = w["cells"][0] * w["cells"][1] * s * n ** 2
-        jv_launch_ms = prof["jv"]["ms"] / max(prof["jv"]["launches"], 1)
+        # average over the Jacobian-vector products actually computed (launches enqueued after a
+        # device-driven GMRES cycle ended return at once and are not counted as products)
+        jv_count = sum(st["jv_evals"] for st in stats)
+        jv_launch_ms = prof["jv"]["ms"] / max(jv_count, 1)
         jv_flops = algorithmic_flops_per_node("euler", 2, n, s, "jv") * nodes
         achieved = jv_flops / (jv_launch_ms * 1e-3) / 1e12
         traffic = _ncu_traffic()

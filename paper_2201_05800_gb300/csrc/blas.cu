@@ -1,6 +1,10 @@
 // Vector kernels of the Newton-GMRES slab solver (see blas.cuh).
 #include "blas.cuh"
 
+#include <stdint.h>
+
+#include <type_traits>
+
 namespace stdg {
 
 namespace {
@@ -44,7 +48,24 @@ __global__ void __launch_bounds__(kRedThreads) multidot_kernel(const TV* __restr
 #pragma unroll
   for (int i = 0; i < K; ++i) acc[i] = CT(0);
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < L; idx += stride) {
+  size_t start = 0;
+  if constexpr (std::is_same<TV, float>::value && std::is_same<TW, float>::value) {
+    // FP32 rows: 16-byte loads (four values per load) when every row is 16-byte aligned
+    if (ld % 4 == 0 && ((uintptr_t)V & 15) == 0 && ((uintptr_t)w & 15) == 0) {
+      const size_t L4 = L / 4;
+      const float4* w4 = reinterpret_cast<const float4*>(w);
+      for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < L4; q += stride) {
+        const float4 wv = w4[q];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          const float4 x = reinterpret_cast<const float4*>(V + (size_t)i * ld)[q];
+          acc[i] = fmaf(x.w, wv.w, fmaf(x.z, wv.z, fmaf(x.y, wv.y, fmaf(x.x, wv.x, acc[i]))));
+        }
+      }
+      start = L4 * 4;
+    }
+  }
+  for (size_t idx = start + (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < L; idx += stride) {
     const CT wv = (CT)w[idx];
 #pragma unroll
     for (int i = 0; i < K; ++i) acc[i] = fma((CT)V[(size_t)i * ld + idx], wv, acc[i]);
@@ -66,7 +87,36 @@ __global__ void __launch_bounds__(kRedThreads) update_kernel(TW* __restrict__ w,
   if (threadIdx.x < kMaxDots) cn[threadIdx.x] = threadIdx.x < k ? (CT)(-c.c[threadIdx.x]) : CT(0);
   __syncthreads();
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < L; idx += stride) {
+  size_t start = 0;
+  if constexpr (std::is_same<TV, float>::value && std::is_same<TW, float>::value) {
+    // FP32 rows: 16-byte loads and stores when every row is 16-byte aligned
+    if (ld % 4 == 0 && ((uintptr_t)V & 15) == 0 && ((uintptr_t)w & 15) == 0) {
+      const size_t L4 = L / 4;
+      float4* w4 = reinterpret_cast<float4*>(w);
+      for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < L4; q += stride) {
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        int i = 0;
+        for (; i + 2 <= k; i += 2) {
+          const float4 x = reinterpret_cast<const float4*>(V + (size_t)i * ld)[q];
+          const float4 y = reinterpret_cast<const float4*>(V + (size_t)(i + 1) * ld)[q];
+          a.x = fmaf(cn[i], x.x, a.x); a.y = fmaf(cn[i], x.y, a.y);
+          a.z = fmaf(cn[i], x.z, a.z); a.w = fmaf(cn[i], x.w, a.w);
+          b.x = fmaf(cn[i + 1], y.x, b.x); b.y = fmaf(cn[i + 1], y.y, b.y);
+          b.z = fmaf(cn[i + 1], y.z, b.z); b.w = fmaf(cn[i + 1], y.w, b.w);
+        }
+        if (i < k) {
+          const float4 x = reinterpret_cast<const float4*>(V + (size_t)i * ld)[q];
+          a.x = fmaf(cn[i], x.x, a.x); a.y = fmaf(cn[i], x.y, a.y);
+          a.z = fmaf(cn[i], x.z, a.z); a.w = fmaf(cn[i], x.w, a.w);
+        }
+        float4 o = w4[q];
+        o.x += a.x + b.x; o.y += a.y + b.y; o.z += a.z + b.z; o.w += a.w + b.w;
+        w4[q] = o;
+      }
+      start = L4 * 4;
+    }
+  }
+  for (size_t idx = start + (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < L; idx += stride) {
     CT x0 = CT(0), x1 = CT(0), x2 = CT(0), x3 = CT(0);
     int i = 0;
     for (; i + 4 <= k; i += 4) {
