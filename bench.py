@@ -29,17 +29,21 @@ sys.path.insert(0, ROOT)
 
 METRIC = "space-time GDOF residual evals/s + slab solves/s, p50/p99 latency vs plain GPU"
 UNIT = "GDOF/s"
+# gmres_rtol is the constant inexact-Newton forcing term eta (the paper gives none): 0.05 was the
+# fastest of {1e-5, 1e-4, 1e-3, 1e-2, 2e-2, 5e-2, 1e-1} for this workload on GB300 (21.8 ms vs 33.6 ms
+# per FP64 slab at 1e-3; 7 Newton steps of ~11 GMRES iterations instead of 4 of ~27).  The stopping
+# test, and so the accuracy, is the Newton one (rtol 1e-10) either way.
 WORKLOAD = dict(dim=2, cells=(64, 64), lo=(0.0, 0.0), hi=(10.0, 10.0), N=4, s=4, gamma=1.4, cfl=0.5,
-                newton_rtol=1e-10, gmres_m=30, gmres_rtol=1e-3)
+                newton_rtol=1e-10, gmres_m=30, gmres_rtol=0.05)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x FP64 FMA/clk/SM x flop/FMA x max SM clock
 HBM_PEAK_GBS = 6767.7
 
 
 def _workload_name():
     w = WORKLOAD
-    return "2D Euler isentropic vortex, %dx%d quads on [0,10]^2, N=%d, s=%d, CFL %.1f, JFNK GMRES(%d), " \
-           "Newton rtol %g, FP64" % (w["cells"][0], w["cells"][1], w["N"], w["s"], w["cfl"], w["gmres_m"],
-                                     w["newton_rtol"])
+    return "2D Euler isentropic vortex, %dx%d quads on [0,10]^2, N=%d, s=%d, CFL %.1f, JFNK GMRES(%d) " \
+           "forcing %g, Newton rtol %g, FP64" % (w["cells"][0], w["cells"][1], w["N"], w["s"], w["cfl"],
+                                                  w["gmres_m"], w["gmres_rtol"], w["newton_rtol"])
 
 
 def _vortex_state(coords):
