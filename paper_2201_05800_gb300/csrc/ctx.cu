@@ -231,8 +231,9 @@ int choose_epb(const stdg_ctx* c, int mode, size_t tsize) {
     const long long nblocks = (c->nelem + epb - 1) / epb;
     const long long per_sm = (nblocks + c->sms - 1) / c->sms;
     const double balance = ((double)c->nelem / c->sms) / (double)(per_sm * epb);
+    // idle lanes cost little in a kernel bound by the per-SM FP64 pipe: weigh them half
     const double lanes = (double)std::min(epb * c->nd, 256) / threads;
-    const double score = balance * lanes * (1.0 + 0.1 * (epb - 1) / epb);
+    const double score = balance * (0.5 + 0.5 * lanes) * (1.0 + 0.1 * (epb - 1) / epb);
     if (score > best_score + 1e-9) {
       best_score = score;
       best = epb;
