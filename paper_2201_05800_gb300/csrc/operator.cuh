@@ -2,11 +2,12 @@
 //
 // One CTA owns `epb` consecutive elements and walks the s temporal nodes of
 // their slab.  For every temporal node m:
-//   0. stage the element tiles of node m in shared memory (coalesced loads,
-//      component-planar, node stride padded to an odd count): U (residual),
-//      U + eps v (finite-difference Jv) or U and v (exact Jv)
-//   1. thread per node: f_a(u) and the wave speed |v_a| + c for all
-//      directions a (one reciprocal of rho, one pressure, one sound speed)
+//   0. thread per node: stage the element tiles of node m in shared memory
+//      (coalesced loads, component-planar, node stride padded to an odd count):
+//      U (residual), U + eps v (finite-difference Jv) or U and v (exact Jv), and
+//      evaluate f_a(u) and the wave speed |v_a| + c for all directions a from the
+//      staged values (one reciprocal of rho, one pressure, one sound speed)
+//   1. (viscous term only) gradients of the staged lines
 //   2. thread per node: volume term  -sum_a (2/h_a) (D f_a)      -> smem acc
 //   3. thread per face point, one direction a at a time: Rusanov flux and the
 //      strong-form face correction -(2/h_a)(1/w_end)(H.n - f_a(u).n).  A face
@@ -137,33 +138,32 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
   const T* gtile = (MODE == kModeResidual) ? k.U : k.v;
 
   for (int m = 0; m < s; ++m) {
-    // ---- 0. stage node m of the CTA's elements (coalesced global reads)
+    // ---- 0. stage node m of the CTA's elements (coalesced global reads) and evaluate the
+    //         fluxes f_a(u) and wave speeds |v_a| + c at every node: each thread works on the
+    //         node it staged (one reciprocal of rho, one pressure, one sound speed per node)
     for (int t = tid; t < nel * nd; t += nth) {
       const int el = div_nd(t), node = t - el * nd;
       const size_t g0 = ((size_t)(e0 + el) * s + m) * tnode + (size_t)node * R;
       const size_t so0 = ((size_t)el * R) * ndp + node;
+      V u[R];
 #pragma unroll
       for (int c = 0; c < R; ++c) {
         const size_t g = g0 + c, so = so0 + (size_t)c * ndp;
         if constexpr (MODE == kModeJvFD) {
-          su[so] = fma(ev, k.v[g], k.U[g]);
+          const T x = fma(ev, k.v[g], k.U[g]);
+          su[so] = x;
+          u[c] = x;
         } else if constexpr (MODE == kModeJvExact) {
-          su[so] = k.U[g];
-          sv[so] = k.vscale * k.v[g];
+          const T x = k.U[g], y = k.vscale * k.v[g];
+          su[so] = x;
+          sv[so] = y;
+          u[c] = tile_state<MODE>(x, y);
         } else {
-          su[so] = k.U[g];
+          const T x = k.U[g];
+          su[so] = x;
+          u[c] = tile_state<MODE>(x, T(0));
         }
       }
-    }
-    __syncthreads();
-    // ---- 1. fluxes and wave speeds at every node
-    for (int t = tid; t < nel * nd; t += nth) {
-      const int el = div_nd(t), node = t - el * nd;
-      const size_t so = ((size_t)el * R) * ndp + node;
-      V u[R];
-#pragma unroll
-      for (int c = 0; c < R; ++c)
-        u[c] = tile_state<MODE>(su[so + c * ndp], MODE == kModeJvExact ? sv[so + c * ndp] : T(0));
       V f[DIM][R];
       V lam[DIM];
       P::flux_all_speed(u, f, lam, k);
@@ -175,8 +175,13 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
 #pragma unroll
         for (int c = 0; c < R; ++c) sfe[(a * R + c) * ndp + node] = f[a][c];
       }
-      if constexpr (R == 1) {
-        if (visc) {
+    }
+    __syncthreads();
+    // ---- 1. (viscous term) gradients along every direction from the staged lines
+    if constexpr (R == 1) {
+      if (visc) {
+        for (int t = tid; t < nel * nd; t += nth) {
+          const int el = div_nd(t), node = t - el * nd;
           // gradient along each direction: (2/h_a) sum_j D[i_a][j] u along the line
           const int q1 = div_n(node), q2 = div_n(q1);
           const int idx[3] = {node - q1 * n, q1 - q2 * n, q2};
@@ -195,9 +200,9 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
             sq[((size_t)el * DIM + a) * ndp + node] = q;
           }
         }
+        __syncthreads();
       }
     }
-    __syncthreads();
     // ---- 2. volume term
     for (int t = tid; t < nel * nd; t += nth) {
       const int el = div_nd(t), node = t - el * nd;
