@@ -64,7 +64,10 @@ def _cfl_dt(u, h):
 
 def algorithmic_flops_per_node(eq, d, n, s, mode):
     """Minimal FP64 flops per space-time node of one operator launch (FMA = 2, div = sqrt = 1);
-    face terms counted once per face (d/n face points per node).  Derivation in the design doc."""
+    face terms counted once per face (d/n face points per node).  Euler (r = d + 2): flux and wave
+    speeds 1 div + (2d+3) pressure + 1 + d(d+3); volume d r 2(n+1); temporal coupling 2 r s + r/s;
+    per face point 12 r + (2d+8) + 9 (+ 2r for the perturbed neighbour of the FD Jv); combination
+    2r + r/s (residual) or 4r plus 2r for U + eps v (FD Jv)."""
     r = d + 2 if eq == "euler" else 1
     if eq == "euler":
         flux = 1 + (2 * d + 3) + 1 + d * (d + 3)
@@ -615,10 +618,12 @@ def _serving_leg(stdg, rates, n_req):
             st = c.advance_slab(check=False)
             svc.append(time.perf_counter() - t0)
             seq_status.append(st["status"])
-    for rate in rates:
+    runs = [(str(r), r, 0.0) for r in rates] + [("%d_shared" % rates[len(rates) // 2], rates[len(rates) // 2],
+                                                    SERVE_SHARE_QUANTUM)]
+    for key, rate, quantum in runs:
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
         with stdg.Server(2, stdg.EULER, max(64, n_req), arena) as srv:
-            srv.configure(share_quantum=SERVE_SHARE_QUANTUM, share_max_stride=SERVE_SHARE_MAX_STRIDE)
+            srv.configure(share_quantum=quantum, share_max_stride=SERVE_SHARE_MAX_STRIDE)
             t0 = time.perf_counter()
             tickets = []
             for (d, u0, _), ta in zip(reqs, arrivals):
@@ -636,15 +641,17 @@ def _serving_leg(stdg, rates, n_req):
             seq_lat.append(fin - ta)
         seq_lat.sort()
         pct = lambda v, q: 1e3 * v[min(len(v) - 1, int(q * len(v)))]
-        out["rates"][str(rate)] = {
+        out["rates"][key] = {
             "served": {"p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "solves_per_s": n_req / T,
                        "max_running": cnt["max_running"],
                        "statuses": {str(k): [r["status"] for r in res].count(k)
                                     for k in sorted({r["status"] for r in res})}},
             "sequential": {"p50_ms": pct(seq_lat, 0.5), "p99_ms": pct(seq_lat, 0.99),
                            "solves_per_s": n_req / fin}}
-    out["scheduling"] = {"share_quantum_dof": SERVE_SHARE_QUANTUM, "share_max_stride": SERVE_SHARE_MAX_STRIDE,
-                         "graphs": True, "autotune": False}
+    out["scheduling"] = {"graphs": True, "autotune": False,
+                         "size_aware_sharing": "off, except the '<rate>_shared' run: a request of L DOF advances "
+                                               "every round(L / %g)-th tick (at most %d)" %
+                                               (SERVE_SHARE_QUANTUM, SERVE_SHARE_MAX_STRIDE)}
     out["sequential_path"] = ("stdg_advance_slab per request in arrival order (FP32 exact Jv, point-block "
                               "preconditioner); latencies from the measured service times under the same arrivals")
     out["sequential_statuses"] = {str(k): seq_status.count(k) for k in sorted(set(seq_status))}
