@@ -347,6 +347,15 @@ stdg_status stdg_server_submit(stdg_server* s, const stdg_config_desc* inst, con
  * NULL) are filled and the ticket is released. */
 stdg_status stdg_server_poll(stdg_server* s, unsigned long long ticket, double wait_s, int* done, int* status,
                              stdg_slab_stats* stats, double* u, double* times);
+/* Cancel a request.  A queued request is dropped; a running one releases its slot
+ * before the worker's next round (the other slots are not affected).  The ticket
+ * then reports done with STDG_ERR_CANCELLED; a request that already finished keeps
+ * its result.  STDG_ERR_INVALID_ARG for an unknown (or already polled) ticket. */
+stdg_status stdg_server_cancel(stdg_server* s, unsigned long long ticket);
+/* Bound the submission queue: stdg_server_submit refuses a request with
+ * STDG_ERR_OOM while max_queued requests wait for admission (0 = unbounded,
+ * the default). */
+stdg_status stdg_server_set_queue_limit(stdg_server* s, size_t max_queued);
 /* The batch knobs of stdg_batch_configure, applied before the worker's next round. */
 stdg_status stdg_server_configure(stdg_server* s, double share_quantum, int share_max_stride, int use_graphs,
                                   int autotune);

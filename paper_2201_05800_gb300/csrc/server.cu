@@ -10,6 +10,7 @@
 // A request admitted while others are running joins their launches at the
 // next tick.  Timestamps (submit, admit, done) give queueing and service
 // latency per request.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -69,6 +70,8 @@ struct stdg_server {
   bool cfg_dirty = false;
   double share_quantum = 0.0;
   int share_max_stride = 16, use_graphs = 1, autotune = 0;
+  size_t max_queue = 0;                          // 0: unbounded submission queue
+  std::vector<int> cancel_slots;                 // slots of cancelled requests, released by the worker
 };
 
 namespace {
@@ -111,6 +114,10 @@ void worker_main(stdg_server* s) {
         stdg_batch_configure(s->batch, s->share_quantum, s->share_max_stride, s->use_graphs, s->autotune);
         s->cfg_dirty = false;
       }
+      // slots of cancelled requests: release them (between ticks, before any new admission can
+      // reuse the slot id)
+      for (int slot : s->cancel_slots) stdg_batch_remove(s->batch, slot);
+      s->cancel_slots.clear();
       if (s->running.empty() && s->queue.empty())
         s->cv.wait_for(lk, std::chrono::milliseconds(50), [&] { return s->stop || !s->queue.empty(); });
       if (s->stop) break;
@@ -178,12 +185,17 @@ void worker_main(stdg_server* s) {
       std::vector<double> out;
       {
         std::lock_guard<std::mutex> lk(s->mu);
-        out.resize(s->reqs[sr.second].u.size());
+        auto it = s->reqs.find(sr.second);
+        if (it == s->reqs.end() || it->second.done || s->running.count(sr.first) == 0) continue;  // cancelled
+        out.resize(it->second.u.size());
       }
       const stdg_status gs = stdg_batch_get_state(s->batch, sr.first, out.data(), STDG_HOST);
-      stdg_batch_remove(s->batch, sr.first);
       std::lock_guard<std::mutex> lk(s->mu);
-      Request& r = s->reqs[sr.second];
+      auto it = s->reqs.find(sr.second);
+      if (it == s->reqs.end() || it->second.done || s->running.count(sr.first) == 0) continue;  // cancelled meanwhile
+      stdg_batch_remove(s->batch, sr.first);
+      Request& r = it->second;
+      r.slot = -1;
       r.u.swap(out);
       r.status = gs == STDG_OK ? status : gs;
       r.stats = stats;
@@ -253,6 +265,7 @@ stdg_status stdg_server_submit(stdg_server* s, const stdg_config_desc* d, const 
   r.t_submit = Clock::now();
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->fatal != STDG_OK) return s->fatal;
+  if (s->max_queue && s->queue.size() >= s->max_queue) return STDG_ERR_OOM;  // queue full: refused
   const unsigned long long t = s->next_ticket++;
   s->reqs.emplace(t, std::move(r));
   s->queue.push_back(t);
@@ -281,6 +294,36 @@ stdg_status stdg_server_poll(stdg_server* s, unsigned long long ticket, double w
     times[2] = seconds(r.t_submit, r.t_done);
   }
   s->reqs.erase(it);
+  return STDG_OK;
+}
+
+stdg_status stdg_server_cancel(stdg_server* s, unsigned long long ticket) {
+  if (!s) return STDG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return STDG_ERR_INVALID_ARG;
+  Request& r = it->second;
+  if (r.done) return STDG_OK;  // finished first: the result stands
+  auto q = std::find(s->queue.begin(), s->queue.end(), ticket);
+  if (q != s->queue.end()) {
+    s->queue.erase(q);
+  } else if (r.slot >= 0) {
+    s->running.erase(r.slot);
+    s->cancel_slots.push_back(r.slot);
+    r.slot = -1;
+  }
+  r.done = true;
+  r.status = STDG_ERR_CANCELLED;
+  r.t_done = Clock::now();
+  if (r.t_admit.time_since_epoch().count() == 0) r.t_admit = r.t_done;
+  s->cv.notify_all();
+  return STDG_OK;
+}
+
+stdg_status stdg_server_set_queue_limit(stdg_server* s, size_t max_queued) {
+  if (!s) return STDG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->max_queue = max_queued;
   return STDG_OK;
 }
 

@@ -311,6 +311,8 @@ _BATCH_SIGS.update({
     "stdg_batch_done_slots": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "stdg_batch_configure": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "stdg_server_configure": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "stdg_server_cancel": (ctypes.c_int, [_P, ctypes.c_ulonglong]),
+    "stdg_server_set_queue_limit": (ctypes.c_int, [_P, ctypes.c_size_t]),
     "stdg_server_create": (ctypes.c_int, [ctypes.POINTER(stdg_batch_desc), ctypes.c_int, ctypes.POINTER(_P)]),
     "stdg_server_destroy": (ctypes.c_int, [_P]),
     "stdg_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(stdg_config_desc), _P,
@@ -508,6 +510,16 @@ class Server:
                                              1 if use_graphs else 0, 1 if autotune else 0)
         if st != 0:
             raise StdgError(st, "stdg_server_configure failed")
+
+    def cancel(self, ticket):
+        st = self._lib.stdg_server_cancel(self._h, ticket)
+        if st != 0:
+            raise StdgError(st, "stdg_server_cancel failed")
+
+    def set_queue_limit(self, max_queued):
+        st = self._lib.stdg_server_set_queue_limit(self._h, int(max_queued))
+        if st != 0:
+            raise StdgError(st, "stdg_server_set_queue_limit failed")
 
     def counters(self):
         a, c, t = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0), ctypes.c_ulonglong(0)

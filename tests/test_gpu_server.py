@@ -110,3 +110,34 @@ def test_request_larger_than_arena_is_refused(S):
         t = srv.submit(p.config(**WORK), u0)
         r = srv.poll(t, wait_s=60.0)
     assert r is not None and r["status"] == 2  # STDG_ERR_OOM
+
+
+def test_cancel_queued_and_running_requests(S):
+    """A cancelled request reports STDG_ERR_CANCELLED whether it was queued or running; the
+    other requests finish with their alone results.  A bounded queue refuses submissions."""
+    p, u0 = _vortex(8, 3, 3)
+    u_alone, _ = _alone(S, p, u0)
+    with S.Batch(2, S.EULER, 2, 1 << 20) as probe:
+        need = probe.slot_bytes(p.config(**WORK))
+    with S.Server(2, S.EULER, 8, need + need // 2) as srv:  # one request runs at a time
+        tickets = [srv.submit(p.config(**WORK), u0) for _ in range(4)]
+        srv.cancel(tickets[2])                 # still queued
+        time.sleep(0.05)
+        srv.cancel(tickets[0])                 # running (or, if very fast, finished)
+        results = [srv.poll(t, wait_s=120.0) for t in tickets]
+        srv.set_queue_limit(1)
+        more = [srv.submit(p.config(**WORK), u0)]
+        with pytest.raises(S.StdgError) as e:
+            for _ in range(3):
+                more.append(srv.submit(p.config(**WORK), u0))
+        assert e.value.status == 2  # STDG_ERR_OOM: the queue is full
+        for t in more:
+            r = srv.poll(t, wait_s=120.0)
+            assert r["status"] == 0 and np.array_equal(r["u"], u_alone)
+        assert srv.counters()["fatal"] == 0
+    assert results[2]["status"] == 8  # STDG_ERR_CANCELLED
+    assert results[0]["status"] in (8, 0)
+    if results[0]["status"] == 0:
+        assert np.array_equal(results[0]["u"], u_alone)
+    for r in (results[1], results[3]):
+        assert r["status"] == 0 and np.array_equal(r["u"], u_alone)
