@@ -62,6 +62,13 @@ struct OpArgs {
   const T* uprev;          // previous slab trace, [e][node][c] (kModeResidual)
   T* out;                  // R or Jv (may be null in kModeResidual)
   T* fout;                 // F(U) (kModeResidual, may be null)
+  // kModeResidual with out set, optional: per-block sums |R|^2, |U|^2 and |W^-1 R|^2 at
+  // nrm[block * nrm_stride + 0..2] (W = M_tau if v0w, else I), and W^-1 R written to v0d
+  // (FP64) or v0f (FP32): the Newton norms and the first Krylov vector in the same pass
+  double* nrm;
+  int nrm_stride, v0w;
+  double* v0d;
+  float* v0f;
 };
 
 // Division of a small index by a runtime divisor d without an integer divide:

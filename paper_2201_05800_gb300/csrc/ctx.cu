@@ -59,6 +59,8 @@ struct stdg_ctx {
   double *U = nullptr, *R = nullptr, *F0 = nullptr, *delta = nullptr, *uprev = nullptr;
   double *X1 = nullptr, *X2 = nullptr, *Xs = nullptr, *V = nullptr, *partials = nullptr, *small = nullptr;
   double* hpin = nullptr;
+  double* rpart = nullptr;   // per-block norm sums of the residual kernel
+  int nres_blocks = 1;
   double t = 0.0;
   bool have_slab = false;
   std::string err;
@@ -342,6 +344,33 @@ stdg_status norm2(stdg_ctx* c, const T* x, size_t L, double* out) {
   return STDG_OK;
 }
 
+// Residual of the Newton iterate with its norms from the same pass: returns |R|_2, |U|_2 and
+// |W^-1 R|_2 (W = M_tau with the left temporal-mass scaling, else I) and writes W^-1 R as the
+// first Krylov vector (v0d in FP64 or v0f in FP32, either may be null).
+stdg_status op_residual_norms(stdg_ctx* c, double* v0d, float* v0f, double* res, double* unorm, double* b0) {
+  OpArgs<double> k = c->a64;
+  k.epb = c->epb64[kModeResidual];
+  k.U = c->U;
+  k.uprev = c->uprev;
+  k.out = c->R;
+  k.fout = c->F0;
+  k.nrm = c->rpart;
+  k.nrm_stride = kPartialStride;
+  k.v0w = c->d.precond == STDG_PRECOND_TEMPORAL_MASS ? 1 : 0;
+  k.v0d = v0d;
+  k.v0f = v0f;
+  {
+    Prof p(c, 0);
+    CK(c, launch_operator<double>(c->dim, c->d.equation, kModeResidual, k, c->st));
+  }
+  PK(c, 2, reduce_partials(c->rpart, c->nres_blocks, 3, c->small + 210, c->st));
+  CKS(fetch_small(c, 210, 3));
+  *res = std::sqrt(c->hpin[210]);
+  *unorm = std::sqrt(c->hpin[211]);
+  *b0 = std::sqrt(c->hpin[212]);
+  return STDG_OK;
+}
+
 // delta as the T-typed input of a Jacobian-vector product (the FP32 copy lives in X)
 template <class T> const T* delta_in(stdg_ctx* c, T* X);
 template <> const double* delta_in<double>(stdg_ctx* c, double*) { return c->delta; }
@@ -365,7 +394,7 @@ template <> double fd_base_eps<float>() { return std::sqrt(1.1920928955078125e-0
 // solve are FP64 on the host in both precisions; the basis, the Jacobian-
 // vector products and the per-thread sums of the dot passes are in T.
 template <class T>
-stdg_status gmres(stdg_ctx* c, double eps_u, int* its_out, int* jv_out) {
+stdg_status gmres(stdg_ctx* c, double eps_u, double beta_pre, int* its_out, int* jv_out) {
   const KView<T> kv = view(c, (T*)nullptr);
   const int m = c->d.gmres_m;
   const size_t L = c->slab_len;
@@ -381,9 +410,12 @@ stdg_status gmres(stdg_ctx* c, double eps_u, int* its_out, int* jv_out) {
   // the Newton residual in T (a cast for the mixed path), then b = -(M^-1 (x) I) R (or -R)
   if (!std::is_same<T, double>::value)
     PK(c, 2, (scale_add<double, T>(kv.R, c->R, 1.0, nullptr, 0.0, L, c->st)));
-  PK(c, 2, (tnode_scale_add<T>(Vrow(0), kv.R, 1.0, winv, nullptr, 0.0, c->nelem, c->s, blk, c->st)));
-  double beta0;
-  CKS(norm2<T>(c, Vrow(0), L, &beta0));
+  // V_0 = (M^-1 (x) I) R (or R): written with its norm by the residual kernel when beta_pre >= 0
+  double beta0 = beta_pre;
+  if (beta_pre < 0.0) {
+    PK(c, 2, (tnode_scale_add<T>(Vrow(0), kv.R, 1.0, winv, nullptr, 0.0, c->nelem, c->s, blk, c->st)));
+    CKS(norm2<T>(c, Vrow(0), L, &beta0));
+  }
   const double tol = c->d.gmres_rtol * beta0;
   int its = 0, jvs = 0;
   bool first = true;
@@ -570,6 +602,7 @@ stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ct
     }
   }
   c->nblk = 4 * c->sms;
+  c->nres_blocks = (int)((c->nelem + c->epb64[kModeResidual] - 1) / c->epb64[kModeResidual]);
   const size_t L = c->slab_len, S = c->state_len;
   const size_t nbasis = L * (size_t)(desc->gmres_m + 1);
   const bool pbp = desc->precond == STDG_PRECOND_POINT_BLOCK;
@@ -583,7 +616,8 @@ stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ct
                  (st = alloc(c, &c->X32, L)) || (st = alloc(c, &c->V32, nbasis)))) ||
       (pbp && !mixed && (st = alloc(c, &c->Pinv64, npinv))) ||
       (pbp && mixed && ((st = alloc(c, &c->Pinv32, npinv)) || (st = alloc(c, &c->Z32, L)))) ||
-      (st = alloc(c, &c->partials, (size_t)c->nblk * kPartialStride)) || (st = alloc(c, &c->small, kSmall))) {
+      (st = alloc(c, &c->partials, (size_t)c->nblk * kPartialStride)) || (st = alloc(c, &c->small, kSmall)) ||
+      (st = alloc(c, &c->rpart, (size_t)c->nres_blocks * kPartialStride))) {
     stdg_destroy(c);
     return st;
   }
@@ -740,10 +774,14 @@ stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
   const size_t L = c->slab_len;
   const int blk = c->nd * c->r;
   PK(c, 3, broadcast_slab<double>(c->U, c->uprev, c->nelem, c->s, blk, c->st));
-  CKS(op_residual(c, c->U, c->uprev, c->R, c->F0));
+  const bool mixed0 = c->d.precision == STDG_MIXED_FP32;
+  // the residual kernel also writes the first Krylov vector into the basis of the working
+  // precision and returns |R|, |U| (FD step) and that vector's norm
+  double* v0d = mixed0 ? nullptr : c->V;
+  float* v0f = mixed0 ? c->V32 : nullptr;
+  double res, unorm, b0;
+  CKS(op_residual_norms(c, v0d, v0f, &res, &unorm, &b0));
   ++S.residual_evals;
-  double res;
-  CKS(norm2<double>(c, c->R, L, &res));
   S.res0 = res;
   const double target = std::fmax(c->d.newton_rtol * res, c->d.newton_atol);
   const bool mixed = c->d.precision == STDG_MIXED_FP32;
@@ -758,8 +796,7 @@ stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
       status = fail(c, STDG_ERR_NOT_CONVERGED, "Newton: newton_maxit reached");
       break;
     }
-    double nu;
-    CKS(norm2<double>(c, c->U, L, &nu));
+    const double nu = unorm;
     int its = 0, jvs = 0;
     if (c->d.precond == STDG_PRECOND_POINT_BLOCK) {
       if (mixed) PK(c, 4, (pb_build<float>(c->dim, c->d.equation, c->a64, c->U, c->Pinv32, c->st)));
@@ -770,16 +807,15 @@ stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
       // FP64 residual below refines (iterative refinement)
       PK(c, 2, (scale_add<double, float>(c->U32, c->U, 1.0, nullptr, 0.0, L, c->st)));
       if (c->d.jv_mode == STDG_JV_FD) CKS(op_spatial<float>(c, view(c, (float*)nullptr), c->U32, c->F032));
-      CKS(gmres<float>(c, fd_base_eps<float>() * (1.0 + nu), &its, &jvs));
+      CKS(gmres<float>(c, fd_base_eps<float>() * (1.0 + nu), b0, &its, &jvs));
     } else {
-      CKS(gmres<double>(c, fd_base_eps<double>() * (1.0 + nu), &its, &jvs));
+      CKS(gmres<double>(c, fd_base_eps<double>() * (1.0 + nu), b0, &its, &jvs));
     }
     S.gmres_its += its;
     S.jv_evals += jvs;
     PK(c, 2, (scale_add<double, double>(c->U, c->U, 1.0, c->delta, 1.0, L, c->st)));
-    CKS(op_residual(c, c->U, c->uprev, c->R, c->F0));
+    CKS(op_residual_norms(c, v0d, v0f, &res, &unorm, &b0));
     ++S.residual_evals;
-    CKS(norm2<double>(c, c->R, L, &res));
     ++S.newton_its;
   }
   S.res_final = res;

@@ -81,7 +81,8 @@ __host__ __device__ inline size_t op_smem_bytes(int n, int s, int epb) {
 // when FIXED, else upper bounds (runtime n, s).  Ends with a __syncthreads, so
 // a CTA may call it again for another tile.
 template <int DIM, int EQ, class T, int MODE, int NPX, int NTX, bool FIXED>
-__device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long tile, unsigned char* smem_raw) {
+__device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long tile, unsigned char* smem_raw,
+                                                 double* sums = nullptr) {
   using P = Phys<EQ, DIM>;
   constexpr int R = P::R;
   using V = typename std::conditional<MODE == kModeJvExact, Dual<T>, T>::type;
@@ -162,6 +163,7 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
           const T x = k.U[g];
           su[so] = x;
           u[c] = tile_state<MODE>(x, T(0));
+          if (sums) sums[1] = fma((double)x, (double)x, sums[1]);
         }
       }
       V f[DIM][R];
@@ -426,7 +428,15 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
           // u_prev is only read when R is written (F-only launches pass no u_prev)
           if (k.out) {
             if (m == 0) lin += k.uprev[(size_t)(e0 + el) * tnode + (size_t)node * R + c];
-            k.out[g] = lin + cfac * val(Fv);
+            const T rv = lin + cfac * val(Fv);
+            k.out[g] = rv;
+            if (sums) {
+              const double wv = k.v0w ? (double)rv * (double)k.inv_omega[m] : (double)rv;
+              sums[0] = fma((double)rv, (double)rv, sums[0]);
+              sums[2] = fma(wv, wv, sums[2]);
+              if (k.v0d) k.v0d[g] = wv;
+              if (k.v0f) k.v0f[g] = (float)wv;
+            }
           }
           if (k.fout) k.fout[g] = val(Fv);
         } else if (MODE == kModeJvFD) {
@@ -443,7 +453,28 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
 template <int DIM, int EQ, class T, int MODE, int NPX, int NTX, bool FIXED>
 __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant__ OpArgs<T> k) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  st_operator_tile<DIM, EQ, T, MODE, NPX, NTX, FIXED>(k, blockIdx.x, smem_raw);
+  if (MODE == kModeResidual && k.nrm && k.out) {
+    // residual with its norms: per-thread sums, then a fixed-order block sum
+    double sums[3] = {0.0, 0.0, 0.0};
+    st_operator_tile<DIM, EQ, T, MODE, NPX, NTX, FIXED>(k, blockIdx.x, smem_raw, sums);
+    __shared__ double red[256 / 32][3];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      double v = sums[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[wid][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+      k.nrm[(size_t)blockIdx.x * k.nrm_stride + threadIdx.x] = v;
+    }
+  } else {
+    st_operator_tile<DIM, EQ, T, MODE, NPX, NTX, FIXED>(k, blockIdx.x, smem_raw);
+  }
 }
 
 }  // namespace stdg
