@@ -95,6 +95,15 @@ enum { STDG_HOST = 0, STDG_DEVICE = 1 };
  * unscaled ||R||_2. */
 enum { STDG_PRECOND_NONE = 0, STDG_PRECOND_TEMPORAL_MASS = 1, STDG_PRECOND_POINT_BLOCK = 2 };
 
+/* Initial Newton iterate U0 of a slab.  CONSTANT: U0 = 1 (x) u^n.  EXTRAPOLATE: after a
+ * solved slab of the same context, the previous slab's temporal polynomial evaluated at the
+ * new slab's nodes, U0_m = sum_j l_j(tau_m + 2) U_j^prev (Lagrange basis l_j on the LGL nodes:
+ * the temporal factor of the space-time expansion of Eq. StCoeff continued past its slab, with
+ * tau in [-1, 1] on each slab); it is kept only when its residual is
+ * below that of the constant guess.  The Newton target stays max(rtol ||R(1 (x) u^n)||, atol)
+ * in both cases, so the accuracy asked of a slab does not depend on this choice. */
+enum { STDG_PREDICTOR_CONSTANT = 0, STDG_PREDICTOR_EXTRAPOLATE = 1 };
+
 typedef struct {
   int dim;                  /* spatial dimension d, 1..3                                 */
   int cells[3];             /* elements per direction (entries beyond dim ignored), >= 1 */
@@ -118,6 +127,7 @@ typedef struct {
   int precond;              /* STDG_PRECOND_NONE | _TEMPORAL_MASS (default) | _POINT_BLOCK */
   double viscosity;         /* nu >= 0: adds nu Laplace(u) (advection and Burgers only)  */
   double penalty;           /* interior penalty eta; <= 0 means the paper's 10 N^2       */
+  int predictor;            /* STDG_PREDICTOR_CONSTANT (default) | _EXTRAPOLATE          */
 } stdg_config_desc;
 
 typedef struct {
@@ -125,7 +135,7 @@ typedef struct {
   int gmres_its;            /* GMRES iterations summed over the Newton steps             */
   int residual_evals;       /* FP64 residual evaluations                                 */
   int jv_evals;             /* Jacobian-vector products                                  */
-  double res0;              /* ||R(U0)||_2 with U0 = 1 (x) u^n                           */
+  double res0;              /* ||R(1 (x) u^n)||_2, the constant guess's residual          */
   double res_final;         /* ||R(U)||_2 at exit                                        */
 } stdg_slab_stats;
 
@@ -201,11 +211,12 @@ stdg_status stdg_lodg_residual(stdg_ctx* ctx, const double* U, const double* u_p
  * the library allocates the P^-1 storage of the context on the first call. */
 stdg_status stdg_precond_apply(stdg_ctx* ctx, const double* U, const double* v, double* z, int ptr_kind);
 
-/* Kernel timing inside the library: when enabled, every kernel launch is
- * bracketed by CUDA events on the context stream and its device time is
- * summed per class: 0 space-time residual / F(U), 1 Jacobian-vector product,
- * 2 Gram-Schmidt and other vector kernels of GMRES, 3 other (slab copies),
- * 4 point-block preconditioner (build and apply). */
+/* Kernel accounting inside the library, per class: 0 space-time residual /
+ * F(U), 1 Jacobian-vector product, 2 Gram-Schmidt and other vector kernels of
+ * GMRES, 3 other (slab copies, predictor), 4 point-block preconditioner (build
+ * and apply).  Launches are always counted; when timing is enabled every
+ * kernel launch is also bracketed by CUDA events on the context stream and its
+ * device time summed (ms stays 0 while disabled). */
 typedef struct {
   int launches[5];
   double ms[5];
@@ -279,8 +290,9 @@ stdg_status stdg_batch_destroy(stdg_batch* b);
 /* Admit one slab problem with initial state u0 (state layout, stdg_state_len
  * values of the problem, host or device pointer).  inst->dim and
  * inst->equation must match the batch; inst->gmres_m (1..31),
- * newton_rtol/atol/maxit and gmres_rtol are used; precision, jv_mode, precond
- * and gmres_maxit are ignored (see above).  *slot receives the slot id.
+ * newton_rtol/atol/maxit and gmres_rtol are used; precision, jv_mode, precond,
+ * predictor (a slot solves one slab from 1 (x) u0) and gmres_maxit are ignored
+ * (see above).  *slot receives the slot id.
  * STDG_ERR_OOM: the arena (or the slot table) is full; nothing changed. */
 stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* inst, const double* u0, int ptr_kind, int* slot);
 /* Run `ticks` ticks (>= 1), then report in *working how many admitted slots

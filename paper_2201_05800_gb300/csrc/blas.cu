@@ -204,6 +204,25 @@ __global__ void broadcast_kernel(T* __restrict__ U, const T* __restrict__ u, lon
   }
 }
 
+// one thread per (element, value of a temporal node): s reads, s writes, coalesced in the value
+__global__ void temporal_mix_kernel(double* __restrict__ Y, const double* __restrict__ X, const StageMatrix E,
+                                    long long nelem, int s, int blk) {
+  const size_t total = (size_t)nelem * blk;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+    const size_t e = idx / blk, q = idx % blk;
+    const double* x = X + e * s * blk + q;
+    double xv[8];
+    for (int j = 0; j < s; ++j) xv[j] = x[(size_t)j * blk];
+    double* y = Y + e * s * blk + q;
+    for (int m = 0; m < s; ++m) {
+      double a = 0.0;
+      for (int j = 0; j < s; ++j) a = fma(E.a[m][j], xv[j], a);
+      y[(size_t)m * blk] = a;
+    }
+  }
+}
+
 template <class T>
 __global__ void extract_kernel(T* __restrict__ u, const T* __restrict__ U, long long nelem, int s, int blk) {
   const size_t total = (size_t)nelem * blk;
@@ -305,6 +324,13 @@ cudaError_t lodg_combine(double* R, const double* U, const double* F, const doub
 template <class T>
 cudaError_t broadcast_slab(T* U, const T* u, long long nelem, int s, int blk, cudaStream_t st) {
   broadcast_kernel<T><<<grid_for((size_t)nelem * s * blk), 256, 0, st>>>(U, u, nelem, s, blk);
+  return cudaGetLastError();
+}
+
+cudaError_t temporal_mix(double* Y, const double* X, const StageMatrix& E, long long nelem, int s, int blk,
+                         cudaStream_t st) {
+  if (s < 1 || s > 8) return cudaErrorInvalidValue;
+  temporal_mix_kernel<<<grid_for((size_t)nelem * blk), 256, 0, st>>>(Y, X, E, nelem, s, blk);
   return cudaGetLastError();
 }
 

@@ -60,6 +60,11 @@ struct StageMatrix {
 cudaError_t lodg_combine(double* R, const double* U, const double* F, const double* u_prev, const StageMatrix& A,
                          double dt, int form, long long nelem, int s, int per_node_block, cudaStream_t st);
 
+// Y[e][m][:] = sum_j E[m][j] X[e][j][:]: a temporal-node mix (E s x s) applied to every
+// element and spatial node; Y and X must not overlap
+cudaError_t temporal_mix(double* Y, const double* X, const StageMatrix& E, long long nelem, int s, int per_node_block,
+                         cudaStream_t st);
+
 // U[e][m][:] = u[e][:] for all m (initial guess 1 (x) u^n)
 template <class T>
 cudaError_t broadcast_slab(T* U, const T* u, long long nelem, int s, int per_node_block, cudaStream_t st);

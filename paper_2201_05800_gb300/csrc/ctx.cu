@@ -63,6 +63,7 @@ struct stdg_ctx {
   int nres_blocks = 1;
   double t = 0.0;
   bool have_slab = false;
+  StageMatrix ext{};  // U0_m = sum_j ext[m][j] U_j of the previous slab (l_j(tau_m + 2))
   std::string err;
   // kernel timing (stdg_profile_*)
   bool prof = false;
@@ -105,6 +106,7 @@ struct Prof {
   int cls;
   cudaEvent_t a = nullptr;
   Prof(stdg_ctx* ctx, int k) : c(ctx), cls(k) {
+    ++c->prof_launches[cls];  // counted whether or not timing is on
     if (c->prof && (a = take_event(c))) cudaEventRecord(a, c->st);
   }
   ~Prof() {
@@ -125,7 +127,6 @@ void prof_collect(stdg_ctx* c) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, x.second.first, x.second.second) == cudaSuccess) {
       c->prof_ms[x.first] += ms;
-      c->prof_launches[x.first] += 1;
     } else {
       cudaGetLastError();
     }
@@ -194,6 +195,8 @@ stdg_status validate(const stdg_config_desc* d, std::string* why) {
   if (d->precond != STDG_PRECOND_NONE && d->precond != STDG_PRECOND_TEMPORAL_MASS &&
       d->precond != STDG_PRECOND_POINT_BLOCK)
     return bad("unknown precond");
+  if (d->predictor != STDG_PREDICTOR_CONSTANT && d->predictor != STDG_PREDICTOR_EXTRAPOLATE)
+    return bad("unknown predictor");
   return STDG_OK;
 }
 
@@ -559,6 +562,7 @@ void stdg_config_default(stdg_config_desc* d) {
   d->gmres_maxit = 300;
   d->hbm_budget_bytes = 0;
   d->precond = STDG_PRECOND_TEMPORAL_MASS;
+  d->predictor = STDG_PREDICTOR_CONSTANT;
 }
 
 stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ctx** out) {
@@ -593,6 +597,18 @@ stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ct
   c->slab_len = c->state_len * c->s;
   fill_args(c, c->a64);
   fill_args(c, c->a32);
+  {
+    // Lagrange basis of the temporal LGL nodes evaluated one slab later: l_j(tau_m + 2)
+    double tau[16], om[16];
+    lgl_rule(c->s, tau, om);
+    for (int m = 0; m < c->s; ++m)
+      for (int j = 0; j < c->s; ++j) {
+        double l = 1.0;
+        for (int q = 0; q < c->s; ++q)
+          if (q != j) l *= (tau[m] + 2.0 - tau[q]) / (tau[j] - tau[q]);
+        c->ext.a[m][j] = l;
+      }
+  }
   for (int mode = 0; mode < 3; ++mode) {
     c->epb64[mode] = choose_epb(c, mode, sizeof(double));
     c->epb32[mode] = choose_epb(c, mode, sizeof(float));
@@ -773,6 +789,9 @@ stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
   std::memset(&S, 0, sizeof(S));
   const size_t L = c->slab_len;
   const int blk = c->nd * c->r;
+  // extrapolated guess from the previous slab (kept in X1 until the constant guess is scored)
+  const bool extrap = c->d.predictor == STDG_PREDICTOR_EXTRAPOLATE && c->have_slab;
+  if (extrap) PK(c, 3, temporal_mix(c->X1, c->U, c->ext, c->nelem, c->s, blk, c->st));
   PK(c, 3, broadcast_slab<double>(c->U, c->uprev, c->nelem, c->s, blk, c->st));
   const bool mixed0 = c->d.precision == STDG_MIXED_FP32;
   // the residual kernel also writes the first Krylov vector into the basis of the working
@@ -783,7 +802,24 @@ stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
   CKS(op_residual_norms(c, v0d, v0f, &res, &unorm, &b0));
   ++S.residual_evals;
   S.res0 = res;
+  // the target is relative to the constant guess whichever iterate the solve starts from
   const double target = std::fmax(c->d.newton_rtol * res, c->d.newton_atol);
+  if (extrap && res > target) {
+    CK(c, cudaMemcpyAsync(c->U, c->X1, L * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    double res_e, unorm_e, b0_e;
+    CKS(op_residual_norms(c, v0d, v0f, &res_e, &unorm_e, &b0_e));
+    ++S.residual_evals;
+    if (std::isfinite(res_e) && res_e < res) {
+      res = res_e;
+      unorm = unorm_e;
+      b0 = b0_e;
+    } else {
+      // the extrapolation is worse: back to the constant guess
+      PK(c, 3, broadcast_slab<double>(c->U, c->uprev, c->nelem, c->s, blk, c->st));
+      CKS(op_residual_norms(c, v0d, v0f, &res, &unorm, &b0));
+      ++S.residual_evals;
+    }
+  }
   const bool mixed = c->d.precision == STDG_MIXED_FP32;
   stdg_status status = STDG_OK;
   while (true) {

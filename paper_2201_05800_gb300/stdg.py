@@ -19,6 +19,7 @@ FP64, MIXED_FP32 = 0, 1
 JV_FD, JV_EXACT = 0, 1
 HOST, DEVICE = 0, 1
 PRECOND_NONE, PRECOND_TEMPORAL_MASS, PRECOND_POINT_BLOCK = 0, 1, 2
+PREDICTOR_CONSTANT, PREDICTOR_EXTRAPOLATE = 0, 1
 
 STATUS = {0: "STDG_OK", 1: "STDG_ERR_INVALID_ARG", 2: "STDG_ERR_OOM", 3: "STDG_ERR_CUDA",
           4: "STDG_ERR_NOT_CONVERGED", 5: "STDG_ERR_GMRES_BREAKDOWN", 6: "STDG_ERR_NAN",
@@ -35,7 +36,8 @@ class stdg_config_desc(ctypes.Structure):
                 ("newton_maxit", ctypes.c_int), ("gmres_m", ctypes.c_int),
                 ("gmres_rtol", ctypes.c_double), ("gmres_maxit", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("precond", ctypes.c_int),
-                ("viscosity", ctypes.c_double), ("penalty", ctypes.c_double)]
+                ("viscosity", ctypes.c_double), ("penalty", ctypes.c_double),
+                ("predictor", ctypes.c_int)]
 
 
 class stdg_slab_stats(ctypes.Structure):
@@ -117,7 +119,10 @@ def config_default():
 def make_config(**kw):
     """stdg_config_desc from defaults overridden by keyword arguments (sequences for arrays)."""
     d = config_default()
+    names = {f[0] for f in stdg_config_desc._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise KeyError(f"stdg_config_desc has no field {k!r}")
         if k in ("cells", "lo", "hi", "adv_vel"):
             arr = getattr(d, k)
             for i, x in enumerate(v):
