@@ -1,5 +1,6 @@
 // Vector kernels of the Newton-GMRES slab solver (see blas.cuh).
 #include "blas.cuh"
+#include "warp_scatter.cuh"
 
 #include <stdint.h>
 
@@ -9,22 +10,20 @@ namespace stdg {
 
 namespace {
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Block-reduce K accumulators and store them at out[0..K).
+// Block-reduce K accumulators (FP64 adds: about K per lane for the warp step) and store
+// them at out[0..K).
 template <int K>
 __device__ __forceinline__ void block_store(const double (&acc)[K], double* out) {
+  static_assert(K >= 1 && K <= 32, "at most 32 rows");
+  constexpr int KP = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
   __shared__ double red[kRedThreads / 32][K];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double a[KP];
 #pragma unroll
-  for (int i = 0; i < K; ++i) {
-    double v = warp_sum(acc[i]);
-    if (lane == 0) red[wid][i] = v;
-  }
+  for (int i = 0; i < KP; ++i) a[i] = i < K ? acc[i] : 0.0;
+  int row = 0;
+  WarpScatter<KP, 16>::run(a, lane, row);
+  if ((lane & (32 / KP - 1)) == 0 && row < K) red[wid][row] = a[0];
   __syncthreads();
   if (threadIdx.x < K) {
     double v = 0.0;
@@ -115,6 +114,25 @@ __global__ void __launch_bounds__(kRedThreads) update_kernel(TW* __restrict__ w,
       }
       start = L4 * 4;
     }
+  }
+  if constexpr (std::is_same<CT, double>::value && std::is_same<WT, double>::value) {
+    // FP64 basis and w: one FMA chain from w (k FMAs per element, no extra adds on the
+    // FP64 pipe); four loads issued ahead of their FMAs
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < L; idx += stride) {
+      double acc = (double)w[idx];
+      int i = 0;
+      for (; i + 4 <= k; i += 4) {
+        const double v0 = (double)V[(size_t)i * ld + idx], v1 = (double)V[(size_t)(i + 1) * ld + idx];
+        const double v2 = (double)V[(size_t)(i + 2) * ld + idx], v3 = (double)V[(size_t)(i + 3) * ld + idx];
+        acc = fma(cn[i], v0, acc);
+        acc = fma(cn[i + 1], v1, acc);
+        acc = fma(cn[i + 2], v2, acc);
+        acc = fma(cn[i + 3], v3, acc);
+      }
+      for (; i < k; ++i) acc = fma(cn[i], (double)V[(size_t)i * ld + idx], acc);
+      w[idx] = (TW)acc;
+    }
+    return;
   }
   for (size_t idx = start + (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < L; idx += stride) {
     CT x0 = CT(0), x1 = CT(0), x2 = CT(0), x3 = CT(0);

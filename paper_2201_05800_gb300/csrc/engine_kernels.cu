@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include "engine.cuh"
+#include "warp_scatter.cuh"
 
 namespace stdg {
 
@@ -73,15 +74,13 @@ __device__ __forceinline__ void dot_rows(const SlotBuf& b, size_t v0, size_t v1,
       for (int i = 0; i < G; ++i)
         if (g0 + i < k) acc[i] = fmaf(b.V[(size_t)(g0 + i) * b.L + v], w0, acc[i]);
     }
+    // warp sums of the group's rows by a reduce-scatter (rows past k are zeros)
+    double d[G];
 #pragma unroll
-    for (int i = 0; i < G; ++i) {
-      if (g0 + i < k) {
-        double d = (double)acc[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-        if (lane == 0) red[wid][g0 + i] = d;
-      }
-    }
+    for (int i = 0; i < G; ++i) d[i] = g0 + i < k ? (double)acc[i] : 0.0;
+    int row = 0;
+    WarpScatter<G, 16>::run(d, lane, row);
+    if ((lane & (32 / G - 1)) == 0 && g0 + row < k) red[wid][g0 + row] = d[0];
   }
   __syncthreads();
   if (threadIdx.x < k) {
@@ -95,7 +94,7 @@ __device__ __forceinline__ void dot_rows(const SlotBuf& b, size_t v0, size_t v1,
 // partials[item][i], i < k: |R|^2 over the chunk (kPhResid) or V_i . w with
 // w = V_{j+1} (kPhArnoldi, kPhReorth; k = j + 2, per-thread sums in FP32 as in
 // the single-slab mixed path, cross-thread sums in FP64 in a fixed order).
-__global__ void __launch_bounds__(kEngThreads) eng_dot_kernel(const __grid_constant__ EngLaunch L) {
+__global__ void __launch_bounds__(kEngThreads, 4) eng_dot_kernel(const __grid_constant__ EngLaunch L) {
   __shared__ double red[kEngThreads / 32][kEngRows];
   const int n = *L.n_chunk_items;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
