@@ -683,7 +683,7 @@ def _density_wave_leg(stdg, stream, slabs=2):
     K, N, s = 32, 3, 3
     base = dict(dim=3, cells=[K, K, K], lo=[0, 0, 0], hi=[1, 1, 1], N=N, s=s, equation=stdg.EULER, gamma=1.4,
                 dt=1.0, newton_rtol=1e-10, gmres_m=30, gmres_rtol=WORKLOAD["gmres_rtol"], newton_maxit=30,
-                gmres_maxit=600)
+                gmres_maxit=600, predictor=WORKLOAD["predictor"])
     d = stdg.make_config(**base)
     with stdg.Context(d, stream.cuda_stream) as c:
         X = c.node_coordinates()
@@ -694,7 +694,8 @@ def _density_wave_leg(stdg, stream, slabs=2):
     lam = float(np.max(np.abs(ur[:, 1] / rho) + np.sqrt(1.4 * p / rho)))
     dt = 0.5 * (1.0 / K) / lam
     out = {"workload": "3D Euler density wave on the periodic unit cube, 32^3 hexes, N=3, s=3, CFL 0.5 "
-                       "(dt = %.6g), Newton rtol 1e-10, GMRES(30) forcing %g" % (dt, WORKLOAD["gmres_rtol"])}
+                       "(dt = %.6g), Newton rtol 1e-10, GMRES(30) forcing %g, %s initial guess" % (
+                           dt, WORKLOAD["gmres_rtol"], "extrapolated" if WORKLOAD["predictor"] else "constant")}
     finals = {}
     for name, prec, jv in (("fp64", stdg.FP64, stdg.JV_FD), ("mixed_fp32", stdg.MIXED_FP32, stdg.JV_EXACT)):
         dd = stdg.make_config(**dict(base, dt=dt, precision=prec, jv_mode=jv))
@@ -742,7 +743,7 @@ def _ncu_traffic():
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
