@@ -67,6 +67,9 @@ struct OpArgs {
   // (FP64) or v0f (FP32): the Newton norms and the first Krylov vector in the same pass
   double* nrm;
   int nrm_stride, v0w;
+  // temporal nodes split over CTAs: CTA b works on element tile b / msplit and on the
+  // temporal nodes m = b % msplit, b % msplit + msplit, ... (0 or 1: one CTA per tile)
+  int msplit;
   double* v0d;
   float* v0f;
 };

@@ -47,6 +47,8 @@ struct stdg_ctx {
   OpArgs<float> a32;
   int epb64[3] = {1, 1, 1};
   int epb32[3] = {1, 1, 1};
+  int msp64[3] = {1, 1, 1};  // temporal split of the operator launches (OpArgs::msplit)
+  int msp32[3] = {1, 1, 1};
   int nblk = 1;
   // FP32 buffers of the mixed-precision Krylov solve (STDG_MIXED_FP32 only)
   float *U32 = nullptr, *F032 = nullptr, *R32 = nullptr, *X32 = nullptr, *V32 = nullptr;
@@ -217,13 +219,20 @@ stdg_status alloc(stdg_ctx* c, T** p, size_t count) {
   return STDG_OK;
 }
 
-// Elements per CTA of the operator kernel.  The kernel is throughput bound per
-// SM, so its time follows the most loaded SM: ceil(blocks / SMs) * epb
-// elements.  Score = load balance x active lanes x a small bonus for faces
-// shared inside a CTA; CTAs are limited by shared memory (228 KB per SM,
-// 1 KB reserved per CTA), threads (2048 per SM) and 32 CTAs per SM.
-int choose_epb(const stdg_ctx* c, int mode, size_t tsize) {
-  int best = 1;
+// Elements per CTA (epb) and temporal split (msplit) of the operator kernel.  The
+// kernel is throughput bound per SM, so its time follows the most loaded SM: the work
+// units are (element, temporal node) pairs and a CTA holds epb * s / msplit of them.
+// For the FP64 FD Jacobian-vector product (FP64-pipe bound), when the element tiles give
+// fewer than 32 warps per SM (the residency of these 64-register kernels), each CTA takes
+// one temporal node of its tile (msplit = s): s times as many CTAs, each with 1/s of the
+// work, so that the resident warps keep the FP64 pipe busy through the barriers (measured
+// on the 64^2 vortex: 0.137 -> 0.133 ms per launch).  The FP32 exact product (latency
+// bound) and the residual with its norms were slower split (27.1 -> 27.9 us, +5%).
+// Score = load balance x active lanes x a small bonus for faces shared inside a CTA;
+// CTAs are limited by shared memory (228 KB per SM, 1 KB reserved per CTA), threads
+// (2048 per SM) and 32 CTAs per SM.
+int choose_epb(const stdg_ctx* c, int mode, size_t tsize, int* msplit) {
+  int best = 1, best_ms = 1;
   double best_score = -1.0;
   const int max_epb = std::max(1, 256 / c->nd);
   for (int epb = 1; epb <= max_epb && epb <= c->nelem; ++epb) {
@@ -233,17 +242,23 @@ int choose_epb(const stdg_ctx* c, int mode, size_t tsize) {
     threads = (threads + 31) / 32 * 32;
     const int bps = std::min({(int)(233472 / (smem + 1024)), 2048 / threads, 32});
     if (bps < 1) break;
-    const long long nblocks = (c->nelem + epb - 1) / epb;
+    const long long tiles = (c->nelem + epb - 1) / epb;
+    const bool may_split = mode == kModeJvFD && tsize == sizeof(double);
+    const int ms = may_split && tiles * (threads / 32) < 32LL * c->sms ? c->s : 1;
+    const long long nblocks = tiles * ms;
     const long long per_sm = (nblocks + c->sms - 1) / c->sms;
-    const double balance = ((double)c->nelem / c->sms) / (double)(per_sm * epb);
+    const double balance =
+        ((double)c->nelem * c->s / c->sms) / ((double)per_sm * epb * ((double)c->s / ms));
     // idle lanes cost little in a kernel bound by the per-SM FP64 pipe: weigh them half
     const double lanes = (double)std::min(epb * c->nd, 256) / threads;
     const double score = balance * (0.5 + 0.5 * lanes) * (1.0 + 0.1 * (epb - 1) / epb);
     if (score > best_score + 1e-9) {
       best_score = score;
       best = epb;
+      best_ms = ms;
     }
   }
+  *msplit = best_ms;
   return best;
 }
 
@@ -251,6 +266,7 @@ int choose_epb(const stdg_ctx* c, int mode, size_t tsize) {
 stdg_status op_residual(stdg_ctx* c, const double* U, const double* uprev, double* out, double* fout) {
   OpArgs<double> k = c->a64;
   k.epb = c->epb64[kModeResidual];
+  k.msplit = c->msp64[kModeResidual];
   k.U = U;
   k.uprev = uprev;
   k.out = out;
@@ -266,6 +282,7 @@ template <class T>
 struct KView {
   const OpArgs<T>* args;
   const int* epb;
+  const int* msp;
   T* U;   // Newton iterate in T
   T* F0;  // F(U) in T (FD Jv)
   T* R;   // Newton residual in T
@@ -276,10 +293,10 @@ struct KView {
 };
 
 KView<double> view(stdg_ctx* c, double*) {
-  return {&c->a64, c->epb64, c->U, c->F0, c->R, c->X1, c->V, c->X2, c->Pinv64};
+  return {&c->a64, c->epb64, c->msp64, c->U, c->F0, c->R, c->X1, c->V, c->X2, c->Pinv64};
 }
 KView<float> view(stdg_ctx* c, float*) {
-  return {&c->a32, c->epb32, c->U32, c->F032, c->R32, c->X32, c->V32, c->Z32, c->Pinv32};
+  return {&c->a32, c->epb32, c->msp32, c->U32, c->F032, c->R32, c->X32, c->V32, c->Z32, c->Pinv32};
 }
 
 // F(U) only, in precision T (FD Jv base point of the mixed path)
@@ -287,6 +304,7 @@ template <class T>
 stdg_status op_spatial(stdg_ctx* c, const KView<T>& kv, const T* U, T* fout) {
   OpArgs<T> k = *kv.args;
   k.epb = kv.epb[kModeResidual];
+  k.msplit = kv.msp[kModeResidual];
   k.U = U;
   k.uprev = nullptr;
   k.out = nullptr;
@@ -304,6 +322,7 @@ stdg_status op_jv_t(stdg_ctx* c, const KView<T>& kv, const T* U, const T* F0, co
   const int mode = c->d.jv_mode == STDG_JV_EXACT ? kModeJvExact : kModeJvFD;
   OpArgs<T> k = *kv.args;
   k.epb = kv.epb[mode];
+  k.msplit = kv.msp[mode];
   k.U = U;
   k.v = v;
   k.F0 = F0;
@@ -353,6 +372,7 @@ stdg_status norm2(stdg_ctx* c, const T* x, size_t L, double* out) {
 stdg_status op_residual_norms(stdg_ctx* c, double* v0d, float* v0f, double* res, double* unorm, double* b0) {
   OpArgs<double> k = c->a64;
   k.epb = c->epb64[kModeResidual];
+  k.msplit = c->msp64[kModeResidual];
   k.U = c->U;
   k.uprev = c->uprev;
   k.out = c->R;
@@ -610,15 +630,16 @@ stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ct
       }
   }
   for (int mode = 0; mode < 3; ++mode) {
-    c->epb64[mode] = choose_epb(c, mode, sizeof(double));
-    c->epb32[mode] = choose_epb(c, mode, sizeof(float));
+    c->epb64[mode] = choose_epb(c, mode, sizeof(double), &c->msp64[mode]);
+    c->epb32[mode] = choose_epb(c, mode, sizeof(float), &c->msp32[mode]);
     if (operator_smem_bytes(c->dim, c->r, sizeof(double), mode, c->n, c->s, c->epb64[mode]) > kSmemLimit) {
       delete c;
       return STDG_ERR_UNSUPPORTED;
     }
   }
   c->nblk = 4 * c->sms;
-  c->nres_blocks = (int)((c->nelem + c->epb64[kModeResidual] - 1) / c->epb64[kModeResidual]);
+  c->nres_blocks = (int)((c->nelem + c->epb64[kModeResidual] - 1) / c->epb64[kModeResidual]) *
+                   c->msp64[kModeResidual];
   const size_t L = c->slab_len, S = c->state_len;
   const size_t nbasis = L * (size_t)(desc->gmres_m + 1);
   const bool pbp = desc->precond == STDG_PRECOND_POINT_BLOCK;
@@ -883,6 +904,7 @@ stdg_status stdg_jv_fd_apply(stdg_ctx* c, const double* U, const double* F0, con
   DevGuard g(c->device);
   OpArgs<double> k = c->a64;
   k.epb = c->epb64[kModeJvFD];
+  k.msplit = c->msp64[kModeJvFD];
   k.U = U;
   k.v = v;
   k.F0 = F0;

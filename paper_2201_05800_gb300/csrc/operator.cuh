@@ -82,7 +82,7 @@ __host__ __device__ inline size_t op_smem_bytes(int n, int s, int epb) {
 // a CTA may call it again for another tile.
 template <int DIM, int EQ, class T, int MODE, int NPX, int NTX, bool FIXED>
 __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long tile, unsigned char* smem_raw,
-                                                 double* sums = nullptr) {
+                                                 double* sums = nullptr, int m_first = 0, int m_step = 1) {
   using P = Phys<EQ, DIM>;
   constexpr int R = P::R;
   using V = typename std::conditional<MODE == kModeJvExact, Dual<T>, T>::type;
@@ -138,7 +138,9 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
   // the tile the temporal coupling acts on: U for the residual, v for J v
   const T* gtile = (MODE == kModeResidual) ? k.U : k.v;
 
-  for (int m = 0; m < s; ++m) {
+  // each temporal node is self-contained: F at node m and the linear temporal coupling read
+  // from global memory, so a CTA may take any subset of them
+  for (int m = m_first; m < s; m += m_step) {
     // ---- 0. stage node m of the CTA's elements (coalesced global reads) and evaluate the
     //         fluxes f_a(u) and wave speeds |v_a| + c at every node: each thread works on the
     //         node it staged (one reciprocal of rho, one pressure, one sound speed per node)
@@ -453,10 +455,13 @@ __device__ __forceinline__ void st_operator_tile(const OpArgs<T>& k, long long t
 template <int DIM, int EQ, class T, int MODE, int NPX, int NTX, bool FIXED>
 __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant__ OpArgs<T> k) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ms = k.msplit > 1 ? k.msplit : 1;
+  const long long tile = blockIdx.x / ms;
+  const int m_first = blockIdx.x % ms;
   if (MODE == kModeResidual && k.nrm && k.out) {
     // residual with its norms: per-thread sums, then a fixed-order block sum
     double sums[3] = {0.0, 0.0, 0.0};
-    st_operator_tile<DIM, EQ, T, MODE, NPX, NTX, FIXED>(k, blockIdx.x, smem_raw, sums);
+    st_operator_tile<DIM, EQ, T, MODE, NPX, NTX, FIXED>(k, tile, smem_raw, sums, m_first, ms);
     __shared__ double red[256 / 32][3];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -473,7 +478,7 @@ __global__ void __launch_bounds__(256) st_operator_kernel(const __grid_constant_
       k.nrm[(size_t)blockIdx.x * k.nrm_stride + threadIdx.x] = v;
     }
   } else {
-    st_operator_tile<DIM, EQ, T, MODE, NPX, NTX, FIXED>(k, blockIdx.x, smem_raw);
+    st_operator_tile<DIM, EQ, T, MODE, NPX, NTX, FIXED>(k, tile, smem_raw, nullptr, m_first, ms);
   }
 }
 

@@ -18,7 +18,7 @@ cudaError_t launch_inst(const OpArgs<T>& k, cudaStream_t st) {
   int threads = k.epb * k.nd;
   if (threads > 256) threads = 256;
   threads = (threads + 31) / 32 * 32;
-  const long long blocks = (k.nelem + k.epb - 1) / k.epb;
+  const long long blocks = (k.nelem + k.epb - 1) / k.epb * (k.msplit > 1 ? k.msplit : 1);
   kern<<<(unsigned)blocks, threads, smem, st>>>(k);
   return cudaGetLastError();
 }
