@@ -379,6 +379,10 @@ const char* stdg_last_error(const stdg_ctx* ctx);
 const char* stdg_status_string(stdg_status st);
 /* Library version string. */
 const char* stdg_version(void);
+/* The matrix of STDG_PREDICTOR_EXTRAPOLATE (host only, no GPU needed):
+ * E[m*s + j] = l_j(tau_m + 2) for the s-point temporal LGL rule, 2 <= s <= 5
+ * (s*s doubles written to E, caller-owned).  STDG_ERR_INVALID_ARG otherwise. */
+stdg_status stdg_predictor_matrix(int s, double* E);
 
 #ifdef __cplusplus
 }

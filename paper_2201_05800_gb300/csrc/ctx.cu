@@ -619,15 +619,10 @@ stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ct
   fill_args(c, c->a32);
   {
     // Lagrange basis of the temporal LGL nodes evaluated one slab later: l_j(tau_m + 2)
-    double tau[16], om[16];
-    lgl_rule(c->s, tau, om);
+    double E[64];
+    lagrange_shift_matrix(c->s, 2.0, E);
     for (int m = 0; m < c->s; ++m)
-      for (int j = 0; j < c->s; ++j) {
-        double l = 1.0;
-        for (int q = 0; q < c->s; ++q)
-          if (q != j) l *= (tau[m] + 2.0 - tau[q]) / (tau[j] - tau[q]);
-        c->ext.a[m][j] = l;
-      }
+      for (int j = 0; j < c->s; ++j) c->ext.a[m][j] = E[m * c->s + j];
   }
   for (int mode = 0; mode < 3; ++mode) {
     c->epb64[mode] = choose_epb(c, mode, sizeof(double), &c->msp64[mode]);
@@ -1040,5 +1035,11 @@ const char* stdg_status_string(stdg_status st) {
 }
 
 const char* stdg_version(void) { return "stdg-gb300 0.1"; }
+
+stdg_status stdg_predictor_matrix(int s, double* E) {
+  if (!E || s < 2 || s > 5) return STDG_ERR_INVALID_ARG;
+  lagrange_shift_matrix(s, 2.0, E);
+  return STDG_OK;
+}
 
 }  // extern "C"

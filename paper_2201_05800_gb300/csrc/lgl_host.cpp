@@ -90,4 +90,16 @@ void diff_matrix(int n, const double* x, double* D) {
   }
 }
 
+void lagrange_shift_matrix(int s, double shift, double* E) {
+  double tau[16], w[16];
+  lgl_rule(s, tau, w);
+  for (int m = 0; m < s; ++m)
+    for (int j = 0; j < s; ++j) {
+      double l = 1.0;
+      for (int q = 0; q < s; ++q)
+        if (q != j) l *= (tau[m] + shift - tau[q]) / (tau[j] - tau[q]);
+      E[m * s + j] = l;
+    }
+}
+
 }  // namespace stdg

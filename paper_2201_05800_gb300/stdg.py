@@ -90,6 +90,7 @@ _SIGS = {
     "stdg_last_error": (ctypes.c_char_p, [_P]),
     "stdg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "stdg_version": (ctypes.c_char_p, []),
+    "stdg_predictor_matrix": (ctypes.c_int, [ctypes.c_int, _P]),
 }
 
 
@@ -541,6 +542,16 @@ def version():
 
 def status_string(st):
     return load().stdg_status_string(st).decode()
+
+
+def predictor_matrix(s):
+    """stdg_predictor_matrix: the s x s matrix E[m, j] = l_j(tau_m + 2) of the extrapolated
+    initial iterate (host computation, no GPU needed)."""
+    E = np.zeros((s, s))
+    st = load().stdg_predictor_matrix(s, E.ctypes.data)
+    if st != 0:
+        raise StdgError(st, status_string(st))
+    return E
 
 
 def slab_norm_noalloc(x, out, stream=None):

@@ -45,13 +45,20 @@ def test_struct_layout_matches_header(lib):
 def test_invalid_configs_rejected_without_gpu(lib):
     from paper_2201_05800_gb300 import stdg
     bad = [dict(dim=4), dict(N=0), dict(N=8), dict(s=1), dict(s=6), dict(dt=-1.0), dict(gmres_m=0),
-           dict(gmres_m=64), dict(equation=7), dict(equation=2, dim=3), dict(cells=[0, 1, 1])]
+           dict(gmres_m=64), dict(equation=7), dict(equation=2, dim=3), dict(cells=[0, 1, 1]),
+           dict(predictor=2), dict(predictor=-1), dict(precond=3), dict(viscosity=-1.0)]
     for kw in bad:
         d = stdg.make_config(**kw)
         h = ctypes.c_void_p()
         st = lib.stdg_create(ctypes.byref(d), None, ctypes.byref(h))
         assert st == 1, kw
         assert not h.value
+
+
+def test_make_config_rejects_unknown_fields(lib):
+    from paper_2201_05800_gb300 import stdg
+    with pytest.raises(KeyError):
+        stdg.make_config(predicter=1)
 
 
 def test_status_strings(lib):
