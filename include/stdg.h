@@ -379,6 +379,12 @@ const char* stdg_last_error(const stdg_ctx* ctx);
 const char* stdg_status_string(stdg_status st);
 /* Library version string. */
 const char* stdg_version(void);
+/* The LGL constants the CUDA path is built from (host only, no GPU needed): the
+ * n-point Legendre-Gauss-Lobatto nodes x (ascending on [-1, 1]) and weights w
+ * (Sec. 3.1; in time the same rule with n = s, Sec. 4) and the differentiation
+ * matrix D[i*n + j] = l_j'(x_i) of the Lagrange basis on x (Eq. SBP).
+ * 2 <= n <= 16; x, w: n doubles, D: n*n doubles, caller-owned. */
+stdg_status stdg_lgl_constants(int n, double* x, double* w, double* D);
 /* The matrix of STDG_PREDICTOR_EXTRAPOLATE (host only, no GPU needed):
  * E[m*s + j] = l_j(tau_m + 2) for the s-point temporal LGL rule, 2 <= s <= 5
  * (s*s doubles written to E, caller-owned).  STDG_ERR_INVALID_ARG otherwise. */

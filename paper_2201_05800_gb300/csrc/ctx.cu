@@ -1036,6 +1036,13 @@ const char* stdg_status_string(stdg_status st) {
 
 const char* stdg_version(void) { return "stdg-gb300 0.1"; }
 
+stdg_status stdg_lgl_constants(int n, double* x, double* w, double* D) {
+  if (!x || !w || !D || n < 2 || n > 16) return STDG_ERR_INVALID_ARG;
+  lgl_rule(n, x, w);
+  diff_matrix(n, x, D);
+  return STDG_OK;
+}
+
 stdg_status stdg_predictor_matrix(int s, double* E) {
   if (!E || s < 2 || s > 5) return STDG_ERR_INVALID_ARG;
   lagrange_shift_matrix(s, 2.0, E);

@@ -91,6 +91,7 @@ _SIGS = {
     "stdg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "stdg_version": (ctypes.c_char_p, []),
     "stdg_predictor_matrix": (ctypes.c_int, [ctypes.c_int, _P]),
+    "stdg_lgl_constants": (ctypes.c_int, [ctypes.c_int, _P, _P, _P]),
 }
 
 
@@ -542,6 +543,16 @@ def version():
 
 def status_string(st):
     return load().stdg_status_string(st).decode()
+
+
+def lgl_constants(n):
+    """stdg_lgl_constants: (x, w, D) of the n-point LGL rule as the CUDA path computes them
+    (host computation, no GPU needed)."""
+    x, w, D = np.zeros(n), np.zeros(n), np.zeros((n, n))
+    st = load().stdg_lgl_constants(n, x.ctypes.data, w.ctypes.data, D.ctypes.data)
+    if st != 0:
+        raise StdgError(st, status_string(st))
+    return x, w, D
 
 
 def predictor_matrix(s):
