@@ -163,9 +163,12 @@ stdg_status stdg_get_state(const stdg_ctx* ctx, double* u, int ptr_kind);
 /* Get the last solved slab U (all s time nodes). */
 stdg_status stdg_get_slab(const stdg_ctx* ctx, double* U, int ptr_kind);
 
-/* Solve the current slab (Newton-Krylov from U0 = 1 (x) u^n) and advance:
- * u^n <- U^s, t <- t + dt.  stats may be NULL.  Returns STDG_ERR_NOT_CONVERGED
- * (state still advanced to the last iterate) or STDG_ERR_NAN (state kept). */
+/* Solve the current slab and advance: u^n <- U^s, t <- t + dt.  Newton-Krylov
+ * starts from U0 = 1 (x) u^n, or with STDG_PREDICTOR_EXTRAPOLATE and a slab
+ * solved since the last stdg_set_state from the extrapolated previous slab when
+ * its residual is smaller (the stopping target is relative to ||R(1 (x) u^n)||
+ * either way).  stats may be NULL.  Returns STDG_ERR_NOT_CONVERGED (state still
+ * advanced to the last iterate) or STDG_ERR_NAN (state kept). */
 stdg_status stdg_advance_slab(stdg_ctx* ctx, stdg_slab_stats* stats);
 
 /* R = R(U; u_prev) (slab residual above).  U, R: slab_len; u_prev: state_len. */
