@@ -371,7 +371,7 @@ def gpu_arm(args):
         # ---- the same slabs on the mixed-precision path (FP32 exact Jv and Krylov basis,
         #      FP64 Newton residual and update): throughput and distance to the FP64 path
         mixed = _mixed_path(stdg, desc, u0, args, stream, u_fp64, ws) if "mixed" in args.legs else None
-        batched = _batched_leg(stdg, stream, args.batch_instances, args.batch_sequential) \
+        batched = _batched_leg(stdg, stream, args.batch_instances, args.batch_sequential, args.batch_graphs) \
             if "batched" in args.legs and ws == 1 else None
         served = _serving_leg(stdg, [int(r) for r in args.serve_rates.split(",")], args.serve_requests) \
             if "serving" in args.legs and ws == 1 else None
@@ -556,13 +556,15 @@ def _run_batch(stdg, B, items):
     return [res[i] for i in range(len(items))]
 
 
-def _batched_leg(stdg, stream, n_inst, n_seq):
+def _batched_leg(stdg, stream, n_inst, n_seq, graphs=1):
     import numpy as np
     import torch
     items = _burgers_instances(stdg, n_inst)
     free, _ = torch.cuda.mem_get_info()
     arena = int(free * 0.7)
     with stdg.Batch(2, stdg.BURGERS, n_inst, arena, stream.cuda_stream) as B:
+        if not graphs:
+            B.configure(use_graphs=False)  # plain launches per tick (for per-kernel profiling)
         need = sum(B.slot_bytes(d) for d, _, _ in items)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -590,6 +592,14 @@ def _batched_leg(stdg, stream, n_inst, n_seq):
     diffs = [float(np.linalg.norm(a[2] - b[1]) / np.linalg.norm(b[1])) for a, b in zip(out[:n_seq], seq)
              if a[0] == 0 and b[0] == 0]
     its = [st["gmres_its"] for _, st, _ in out]
+    vs_seq = None
+    if n_seq > 0:
+        vs_seq = {"instances": n_seq, "batched_s": T_small, "sequential_s": T_seq,
+                  "batched_instances_per_s": n_seq / T_small, "sequential_instances_per_s": n_seq / T_seq,
+                  "speedup": T_seq / T_small,
+                  "max_rel_diff_to_sequential": max(diffs) if diffs else None,
+                  "sequential_path": "stdg_advance_slab per instance (context per instance), FP32 exact "
+                                     "Jv + point-block preconditioner, restarted GMRES(30)"}
     return {"workload": "%d independent 2D viscous Burgers instances (seed 1000+i; side in {8,16,32,64}, N 2-6, "
                         "s 2-5, nu log-uniform [1e-3,1e-1]), one slab each, FP32 Krylov + FP64 Newton "
                         "refinement, Newton rtol 1e-10, FGMRES(30) rtol 1e-3" % n_inst,
@@ -598,12 +608,7 @@ def _batched_leg(stdg, stream, n_inst, n_seq):
             "gdof_evals_per_s": evals / T / 1e9,
             "status_counts": {str(k): statuses.count(k) for k in sorted(set(statuses))},
             "gmres_its_mean": float(np.mean(its)), "gmres_its_max": int(max(its)),
-            "vs_sequential": {"instances": n_seq, "batched_s": T_small, "sequential_s": T_seq,
-                              "batched_instances_per_s": n_seq / T_small, "sequential_instances_per_s": n_seq / T_seq,
-                              "speedup": T_seq / T_small,
-                              "max_rel_diff_to_sequential": max(diffs) if diffs else None,
-                              "sequential_path": "stdg_advance_slab per instance (context per instance), FP32 exact "
-                                                 "Jv + point-block preconditioner, restarted GMRES(30)"}}
+            "graphs": bool(graphs), "vs_sequential": vs_seq}
 
 
 SERVE_SHARE_QUANTUM = 262144.0  # DOF: a request of L DOF advances every round(L / quantum)-th tick (<= 16)
@@ -752,6 +757,8 @@ def main():
     ap.add_argument("--batch-instances", type=int, default=4096)
     ap.add_argument("--batch-sequential", type=int, default=48,
                     help="instances solved one at a time for the batched-vs-sequential comparison")
+    ap.add_argument("--batch-graphs", type=int, choices=[0, 1], default=1,
+                    help="0: the batched leg launches its kernels per tick instead of replaying a CUDA graph")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rates", default="100,1000,5000")
     args = ap.parse_args()
