@@ -33,7 +33,8 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_struct_layout_matches_header(lib):
-    """The ctypes mirror of stdg_config_desc has the C layout (size checked against a C probe)."""
+    """stdg_config_default fills the ctypes mirror with the documented defaults (the layout itself
+    is compared with the C header by test_struct_offsets_match_the_c_header)."""
     from paper_2201_05800_gb300 import stdg
     d = stdg.config_default()
     assert d.dim == 1 and d.N == 3 and d.s == 3 and d.gmres_m == 30
@@ -111,3 +112,36 @@ def test_server_without_gpu(lib):
     assert lib.stdg_server_create(ctypes.byref(ok), 4, ctypes.byref(h)) == 3
     assert not h.value
     assert lib.stdg_server_destroy(None) == 1
+
+
+def test_struct_offsets_match_the_c_header(tmp_path):
+    """Size and every field offset of the ctypes mirrors equal those of the C structs, from a C
+    probe compiled against include/stdg.h (catches a field added on one side only)."""
+    import shutil
+    import subprocess
+    from paper_2201_05800_gb300 import stdg
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"stdg_config_desc": stdg.stdg_config_desc, "stdg_slab_stats": stdg.stdg_slab_stats,
+               "stdg_profile": stdg.stdg_profile, "stdg_batch_desc": stdg.stdg_batch_desc}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "stdg.h"', "int main(void) {"]
+    for name, cls in mirrors.items():
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in cls._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    for name, cls in mirrors.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
