@@ -235,8 +235,10 @@ stdg_status stdg_profile_read(stdg_ctx* ctx, stdg_profile* out, int reset);
  * scratch of a context), for instance a host whose device memory is held
  * entirely by its own pool allocator, or a latency-critical loop that must not
  * call cudaMalloc/cudaFree (cudaFree synchronises the device).  It computes
- * the same value as stdg_slab_norm (FP64 squares, per-block partial sums,
- * fixed-order final sum) for any length up to STDG_NORM_NOALLOC_MAX_LEN.
+ * the same norm as stdg_slab_norm up to FP64 rounding (FP64 squares, per-block
+ * partial sums and a fixed-order final sum, but with its own blocking and a
+ * device square root, so the two may differ in the last bits) for any length
+ * up to STDG_NORM_NOALLOC_MAX_LEN.
  *   x            device pointer to len doubles (may be NULL when len == 0)
  *   out          device pointer to one double, receives the norm
  *   cuda_stream  cudaStream_t the two kernels are enqueued on (NULL = default)
@@ -246,8 +248,15 @@ stdg_status stdg_profile_read(stdg_ctx* ctx, stdg_profile* out, int reset);
  * two streams) race on it and must be ordered by the caller.  Every slot a
  * call reads was written by the same call, so no clearing is needed.  The
  * first call on a device, with that device current, looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Returns STDG_ERR_INVALID_ARG for a NULL pointer or
+ * device address (cudaGetSymbolAddress) and keeps it for the life of the
+ * process; make that first call before any stream capture.  The kept address
+ * is valid only in the device's primary context (the one the CUDA runtime
+ * uses) and only until that device is reset: after a cudaDeviceReset, or with
+ * a driver-API context of the caller's own made current, do not call this
+ * function again in the same process.  An error left pending on the calling
+ * thread by earlier CUDA work is not consumed: the call then launches nothing
+ * and returns STDG_ERR_CUDA, leaving the error for its owner to read.
+ * Returns STDG_ERR_INVALID_ARG for a NULL pointer or
  * len > STDG_NORM_NOALLOC_MAX_LEN (nothing is launched), STDG_ERR_CUDA when the
  * set-up or a launch fails, else STDG_OK once the work is enqueued.  Calls no
  * allocating routine. */

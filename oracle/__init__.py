@@ -21,5 +21,9 @@ stdg     Space-time residual (Eq. DG_vs_RK:DG), method-of-lines Lobatto IIIC
 Every function is FP64 and written for a reader checking it against the paper.
 Parity status: every function listed above is pinned by ``tests/test_oracle_*``
 (closed forms, Appendix B/D values, Tables 1-2 convergence orders, exact
-solutions, invariants, brute force).
+solutions, invariants, brute force).  The Burgers branch of ``physics`` is
+pinned by a finite-difference flux derivative and by the characteristic
+solution of smooth 1D Burgers (order N+1), ``stdg.lgl_weighted_norm`` by exact
+integrals of constants and of polynomials within the LGL exactness
+(``tests/test_oracle_burgers_norm.py``).
 """

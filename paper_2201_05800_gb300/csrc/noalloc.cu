@@ -1,9 +1,11 @@
 // stdg_slab_norm_noalloc: the 2-norm of a device vector without any device
 // allocation, for callers that must not allocate (see include/stdg.h).
 //
-// Same arithmetic as stdg_slab_norm (FP64 squares, per-block partial sums,
-// one fixed-order final reduction), but the per-block partial sums live in a
-// file-scope static __device__ array instead of memory owned by a context.
+// The same norm as stdg_slab_norm up to FP64 rounding: FP64 squares, per-block
+// partial sums and one fixed-order final reduction, but with blocks of 16384
+// values and a device square root (stdg_slab_norm blocks differently and takes
+// the root on the host).  The per-block partial sums live in a file-scope
+// static __device__ array instead of memory owned by a context.
 #include <mutex>
 
 #include "stdg.h"
@@ -59,7 +61,9 @@ __global__ void __launch_bounds__(kThreads) final_kernel(const double* __restric
   if (threadIdx.x == 0) out[0] = sqrt(t);
 }
 
-// Device address of the static partials for the current device, looked up once per device.
+// Device address of the static partials for the current device, looked up once per device
+// and kept: valid in the device's primary context until the device is reset (documented in
+// stdg.h; a reset or a caller-made driver context would need a fresh lookup).
 stdg_status partials_for_current_device(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -84,6 +88,9 @@ stdg_status partials_for_current_device(double** out) {
 extern "C" stdg_status stdg_slab_norm_noalloc(const double* x, size_t len, double* out, void* cuda_stream) {
   if (!out || (len > 0 && !x)) return STDG_ERR_INVALID_ARG;
   if (len > STDG_NORM_NOALLOC_MAX_LEN) return STDG_ERR_INVALID_ARG;
+  // an error pending from earlier work on this thread belongs to its owner: leave it
+  // unconsumed and launch nothing, so that the check after the launches sees only ours
+  if (cudaPeekAtLastError() != cudaSuccess) return STDG_ERR_CUDA;
   double* partials = nullptr;
   stdg_status st = partials_for_current_device(&partials);
   if (st != STDG_OK) return st;
