@@ -170,6 +170,16 @@ def _sum_over_ranks(x, ws):
     return float(t.item())
 
 
+def _build_then_load(ws, rank, build_fn, load_fn):
+    """Rank 0 alone compiles the in-tree library (all ranks share one build folder and one .so, so
+    concurrent builds would race on the object files and the link); every rank loads it after a
+    barrier."""
+    if rank == 0:
+        build_fn()
+    _barrier(ws)
+    return load_fn()
+
+
 # ----------------------------------------------------------------------------- oracle legs
 
 ORACLE_SNIPPET = r"""
@@ -256,8 +266,7 @@ def gpu_arm(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     from paper_2201_05800_gb300 import build, stdg
-    build.build()
-    stdg.load()
+    _build_then_load(ws, rank, build.build, stdg.load)
     stream = torch.cuda.Stream()
     w = WORKLOAD
     desc = stdg.make_config(dim=2, cells=[w["cells"][0], w["cells"][1], 1], lo=[w["lo"][0], w["lo"][1], 0.0],
