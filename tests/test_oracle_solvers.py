@@ -164,6 +164,11 @@ def test_newton_gmres_matches_dense_newton(dim):
                                         gmres_tol=1e-12, gmres_m=60, stats=st)
     nrm = stdg.lgl_weighted_norm(g, U_direct)
     assert stdg.lgl_weighted_norm(g, U_gm - U_direct) <= 1e-12 * nrm
+    # the left temporal-mass scaling changes the Krylov iteration, not the Newton solution
+    st_w = {}
+    U_w = stdg.solve_slab_newton_gmres("stdg", _op(g), u_n, dt, s, rtol=1e-14, atol=1e-15,
+                                       gmres_tol=1e-12, gmres_m=60, stats=st_w, scaling="temporal_mass")
+    assert stdg.lgl_weighted_norm(g, U_w - U_direct) <= 1e-12 * nrm
     U_lodg, _ = stdg.solve_slab_direct("lodg", _op(g), u_n, dt, s)
     assert stdg.lgl_weighted_norm(g, U_lodg - U_direct) <= 1e-12 * nrm
     cons = dgsem.integrate(g, U_direct[s - 1]) - dgsem.integrate(g, u_n)
@@ -172,6 +177,26 @@ def test_newton_gmres_matches_dense_newton(dim):
     st = {}
     U_c = stdg.solve_slab_newton_gmres("stdg", _op(g), const, dt, s, rtol=1e-12, atol=1e-14, stats=st)
     assert st["newton_its"] == 0 and np.max(np.abs(U_c - const)) == 0.0
+
+
+def test_temporal_mass_scaling_is_row_scaling_by_one_over_omega():
+    """The scaled system of scaling="temporal_mass" is exactly diag(1/omega_m) J: its GMRES solution
+    equals the dense solve of the unscaled Newton system (s = 3, one Newton step, tiny 2D Euler)."""
+    g, u_n = _euler_tiny(2)
+    s, dt = 3, 0.02
+    U0 = np.stack([u_n] * s)
+    R = stdg.residual("stdg", _op(g), U0, u_n, dt)
+    J = stdg.jacobian_dense("stdg", _op(g), U0, u_n, dt)
+    d_direct = np.linalg.solve(J, -R.ravel())
+    st = {}
+    U1 = stdg.solve_slab_newton_gmres("stdg", _op(g), u_n, dt, s, rtol=0.0, maxit=1, gmres_tol=1e-13,
+                                      gmres_m=200, stats=st, scaling="temporal_mass")
+    assert st["newton_its"] == 1
+    d_gm = (U1 - U0).ravel()
+    assert np.linalg.norm(d_gm - d_direct) <= 1e-11 * np.linalg.norm(d_direct)
+    # the three temporal weights of s = 3 on [-1, 1]: 1/3, 4/3, 1/3 (Simpson)
+    from oracle import lgl
+    assert np.allclose(lgl.lgl_nodes_weights(3)[1], [1 / 3, 4 / 3, 1 / 3], atol=1e-15)
 
 
 def test_newton_converges_quadratically_with_exact_solves():
