@@ -188,6 +188,15 @@ stdg_status stdg_slab_norm(stdg_ctx* ctx, const double* x, int ptr_kind, double*
  * applied to each time level of the slab U (slab layout in and out). */
 stdg_status stdg_spatial_operator(stdg_ctx* ctx, const double* U, double* F, int ptr_kind);
 
+/* J(U) v in FP32 with forward-mode (exact) derivatives, the product the inner
+ * Krylov solve of STDG_MIXED_FP32 with STDG_JV_EXACT uses (Eq. Jacobian_ST):
+ * ((D_tau^T M_tau - e_s e_s^T) (x) I) v + dt/2 (M_tau (x) I) F'(U) v.  Device
+ * pointers to slab_len floats each (slab layout; U, v 16-byte aligned for the
+ * bulk-copy kernel of the 2D n = 5, s = 4 and 3D n = 4, s = 3 Euler shapes,
+ * else the general kernel runs).  Synchronises the context stream; returns
+ * STDG_ERR_TIMEOUT if a kernel's bounded wait for its staged tile ran out. */
+stdg_status stdg_jv_fp32(stdg_ctx* ctx, const float* U, const float* v, float* Jv);
+
 /* One finite-difference Jacobian-vector launch exactly as GMRES issues it
  * (device pointers only): Jv = ((D_tau^T M_tau - e_s e_s^T) (x) I) v
  * + dt/2 (M_tau (x) I) [F(U + eps v) - F0] / eps, with F0 = F(U) supplied by the

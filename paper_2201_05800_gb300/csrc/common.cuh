@@ -72,7 +72,11 @@ struct OpArgs {
   int msplit;
   double* v0d;
   float* v0f;
+  // error word of kernels with bounded waits (bit 0: a wait gave up), or null
+  unsigned* err;
 };
+
+__host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
 
 // Division of a small index by a runtime divisor d without an integer divide:
 // q = floor(t * ceil(2^32 / d) / 2^32) is exact for t, d < 2^16 (the error term

@@ -62,6 +62,7 @@ struct stdg_ctx {
   double *X1 = nullptr, *X2 = nullptr, *Xs = nullptr, *V = nullptr, *partials = nullptr, *small = nullptr;
   double* hpin = nullptr;
   double* rpart = nullptr;   // per-block norm sums of the residual kernel
+  unsigned* errw = nullptr;  // error word of the kernels with bounded waits (0: none gave up)
   int nres_blocks = 1;
   double t = 0.0;
   bool have_slab = false;
@@ -331,8 +332,29 @@ stdg_status op_jv_t(stdg_ctx* c, const KView<T>& kv, const T* U, const T* F0, co
   k.inv_eps = eps > 0.0 ? (T)(1.0 / eps) : (T)0;
   k.lscale = lscale ? 1 : 0;
   k.out = out;
+  k.err = c->errw;
   Prof p(c, 1);
+  if constexpr (std::is_same<T, float>::value) {
+    if (mode == kModeJvExact) {
+      bool handled = false;
+      CK(c, launch_jv_tangent(c->dim, c->d.equation, k, c->st, &handled));
+      if (handled) return STDG_OK;
+    }
+  }
   CK(c, launch_operator<T>(c->dim, c->d.equation, mode, k, c->st));
+  return STDG_OK;
+}
+
+// The error word of the bounded waits: STDG_ERR_TIMEOUT if a kernel gave up waiting for its
+// staged data (its outputs are then incomplete).  Synchronises the stream.
+stdg_status check_errw(stdg_ctx* c) {
+  unsigned h = 0;
+  CK(c, cudaMemcpyAsync(&h, c->errw, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  if (h) {
+    cudaMemsetAsync(c->errw, 0, sizeof(unsigned), c->st);
+    return fail(c, STDG_ERR_TIMEOUT, "a kernel's bounded wait for its staged tile ran out");
+  }
   return STDG_OK;
 }
 
@@ -649,7 +671,7 @@ stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ct
       (pbp && !mixed && (st = alloc(c, &c->Pinv64, npinv))) ||
       (pbp && mixed && ((st = alloc(c, &c->Pinv32, npinv)) || (st = alloc(c, &c->Z32, L)))) ||
       (st = alloc(c, &c->partials, (size_t)c->nblk * kPartialStride)) || (st = alloc(c, &c->small, kSmall)) ||
-      (st = alloc(c, &c->rpart, (size_t)c->nres_blocks * kPartialStride))) {
+      (st = alloc(c, &c->rpart, (size_t)c->nres_blocks * kPartialStride)) || (st = alloc(c, &c->errw, 4))) {
     stdg_destroy(c);
     return st;
   }
@@ -659,7 +681,8 @@ stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ct
     stdg_destroy(c);
     return STDG_ERR_OOM;
   }
-  if (cudaMemsetAsync(c->uprev, 0, S * sizeof(double), c->st) != cudaSuccess ||
+  if (cudaMemsetAsync(c->errw, 0, 4 * sizeof(unsigned), c->st) != cudaSuccess ||
+      cudaMemsetAsync(c->uprev, 0, S * sizeof(double), c->st) != cudaSuccess ||
       cudaMemsetAsync(c->U, 0, L * sizeof(double), c->st) != cudaSuccess ||
       cudaStreamSynchronize(c->st) != cudaSuccess) {
     cudaGetLastError();
@@ -871,6 +894,10 @@ stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
     ++S.newton_its;
   }
   S.res_final = res;
+  if (status == STDG_OK) {
+    const stdg_status we = check_errw(c);
+    if (we != STDG_OK) status = we;
+  }
   if (status != STDG_ERR_NAN) {
     PK(c, 3, extract_last<double>(c->uprev, c->U, c->nelem, c->s, blk, c->st));
     c->t += c->d.dt;
@@ -891,6 +918,17 @@ stdg_status stdg_spatial_operator(stdg_ctx* c, const double* U, double* F, int k
   CK(c, cudaMemcpyAsync(F, c->X2, c->slab_len * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CK(c, cudaStreamSynchronize(c->st));
   return STDG_OK;
+}
+
+stdg_status stdg_jv_fp32(stdg_ctx* c, const float* U, const float* v, float* Jv) {
+  if (!c || !U || !v || !Jv) return STDG_ERR_INVALID_ARG;
+  DevGuard g(c->device);
+  const int saved = c->d.jv_mode;
+  c->d.jv_mode = STDG_JV_EXACT;
+  const stdg_status st = op_jv_t<float>(c, view(c, (float*)nullptr), U, nullptr, v, 1.0, 0.0, Jv, false);
+  c->d.jv_mode = saved;
+  if (st != STDG_OK) return st;
+  return check_errw(c);
 }
 
 stdg_status stdg_jv_fd_apply(stdg_ctx* c, const double* U, const double* F0, const double* v, double eps,

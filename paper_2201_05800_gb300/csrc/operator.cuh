@@ -52,7 +52,6 @@ __device__ __forceinline__ auto tile_state(T u, T v) {
 template <class T> __device__ __forceinline__ T tangent(Dual<T> x) { return x.d; }
 template <class T> __device__ __forceinline__ T tangent(T x) { return T(0); }
 
-__host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
 
 // Shared-memory footprint (bytes) of one CTA.
 template <int DIM, int R, class T, int MODE>

@@ -83,6 +83,7 @@ _SIGS = {
     "stdg_slab_norm": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "stdg_spatial_operator": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "stdg_jv_fd_apply": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, _P]),
+    "stdg_jv_fp32": (ctypes.c_int, [_P, _P, _P, _P]),
     "stdg_precond_apply": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
     "stdg_lodg_residual": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int]),
     "stdg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -239,6 +240,15 @@ class Context:
         if len({k for _, k in ptrs}) != 1:
             raise TypeError("all buffers must be on the same side (host or device)")
         self._check(self._lib.stdg_jv(self._h, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], ptrs[0][1]))
+        return out
+
+    def jv_fp32(self, U, v, out=None):
+        """stdg_jv_fp32: FP32 exact J(U) v on device float32 tensors (slab layout)."""
+        import torch
+        assert U.dtype == torch.float32 and v.dtype == torch.float32 and U.is_cuda and v.is_cuda
+        out = torch.empty_like(U) if out is None else out
+        self._check(self._lib.stdg_jv_fp32(self._h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr())))
         return out
 
     def spatial_operator(self, U, out=None):
