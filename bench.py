@@ -221,6 +221,151 @@ def run_oracle(steps, dt):
     return res["times"], res["dof"], res["evals_per_step"]
 
 
+# ----------------------------------------------------------------------------- oracle checks
+#
+# The oracle (plain FP64 NumPy, one thread per process) is run after every GPU timing has ended,
+# in worker processes started with "spawn".  It supplies the CPU baseline (timings) and, from the
+# same runs, the error of each benchmarked GPU result against the oracle's own slab solution.
+
+def _cpu_info():
+    """Host CPU model and core counts (for the CPU baseline)."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count()
+    return {"model": model or platform.processor() or platform.machine(), "machine": platform.machine(),
+            "nproc": os.cpu_count(), "usable": usable}
+
+
+def _oracle_env():
+    """One BLAS/OpenMP thread per oracle process (the processes themselves use the cores)."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def _rel_lgl(grid, a, b):
+    from oracle import stdg as ost
+    return float(ost.lgl_weighted_norm(grid, a - b) / ost.lgl_weighted_norm(grid, b))
+
+
+def _oracle_job(job):
+    """One oracle task in a worker process; returns a small dict (errors, times, iterations)."""
+    import numpy as np
+    from oracle import dgsem, physics, stdg as ost
+    from paper_2201_05800_gb300 import inputs
+    kind = job["kind"]
+    t_start = time.perf_counter()
+    if kind == "eval_loop":
+        # per repetition: one FP64 residual and one exact (complex-step) Jv of the full vortex slab
+        w = job["w"]
+        g = dgsem.Grid(2, w["cells"], w["lo"], w["hi"], w["N"], "euler", {"gamma": w["gamma"]})
+        X = g.coordinates()
+        u0 = inputs.isentropic_vortex(X[0], X[1], gamma=w["gamma"], center=(5.0, 5.0))
+        U = np.stack([inputs.perturbed(u0, 100 + m, 1e-3) for m in range(w["s"])])
+        v = inputs.random_array(U.shape, 7)
+        F = lambda x: dgsem.spatial_operator(g, x)
+        times = []
+        for _ in range(job["reps"]):
+            t0 = time.perf_counter()
+            ost.stdg_residual(F, U, u0, job["dt"])
+            ost.jv_exact("stdg", F, U, u0, job["dt"], v)
+            times.append(time.perf_counter() - t0)
+        return {"times": times, "dof": int(U.size), "evals_per_rep": 2}
+    if kind == "vortex_march":
+        # the headline workload's first slabs, each solved by the oracle from the oracle's previous slab
+        w = job["w"]
+        g = dgsem.Grid(2, w["cells"], w["lo"], w["hi"], w["N"], "euler", {"gamma": w["gamma"]})
+        X = g.coordinates()
+        u = inputs.isentropic_vortex(X[0], X[1], gamma=w["gamma"], center=(5.0, 5.0))
+        F = lambda x: dgsem.spatial_operator(g, x)
+        slabs = []
+        for k, ug in enumerate(job["gpu"]):
+            t0 = time.perf_counter()
+            st = {}
+            U = ost.solve_slab_newton_gmres("stdg", F, u, job["dt"], w["s"], rtol=w["newton_rtol"],
+                                            maxit=30, gmres_m=w["gmres_m"], gmres_tol=w["gmres_rtol"],
+                                            gmres_maxit=600, stats=st, scaling="temporal_mass")
+            u = U[w["s"] - 1]
+            slabs.append({"slab": k + 1, "oracle_s": time.perf_counter() - t0, "newton_its": st["newton_its"],
+                          "gmres_its": st["gmres_its"],
+                          "rel_l2_vs_oracle": _rel_lgl(g, ug.reshape(g.state_shape), u)})
+        return {"slabs": slabs}
+    if kind in ("burgers", "vortex_request", "wave3d", "advection1d"):
+        if kind == "burgers":
+            sp = inputs.burgers_instance(job["i"])
+            g = dgsem.Grid(2, (sp["side"],) * 2, (0.0, 0.0), (1.0, 1.0), sp["N"], "burgers",
+                           {"viscosity": sp["nu"]})
+            X = g.coordinates()
+            u = inputs.burgers_fourier(X[0], X[1], sp["seed"])
+            s, dt = sp["s"], 0.5 * (1.0 / sp["side"]) / float(np.max(np.abs(u)))
+            exact = None
+        elif kind == "vortex_request":
+            side, N, s = job["side"], job["N"], job["s"]
+            g = dgsem.Grid(2, (side, side), (0.0, 0.0), (10.0, 10.0), N, "euler", {"gamma": 1.4})
+            X = g.coordinates()
+            u = inputs.isentropic_vortex(X[0], X[1], gamma=1.4, center=(5.0, 5.0))
+            lam = max(float(np.max(physics.wave_speed("euler", u, a, g.params))) for a in range(2))
+            dt = 0.5 * (10.0 / side) / lam
+            exact = None
+        elif kind == "wave3d":
+            K, N, s = job["K"], job["N"], job["s"]
+            g = dgsem.Grid(3, (K, K, K), (0.0,) * 3, (1.0,) * 3, N, "euler", {"gamma": 1.4})
+            X = g.coordinates()
+            u = inputs.density_wave(*X, gamma=1.4)
+            lam = max(float(np.max(physics.wave_speed("euler", u, a, g.params))) for a in range(3))
+            dt = 0.5 * (1.0 / K) / lam
+            exact = lambda t: inputs.density_wave(*X, t=t, gamma=1.4)
+        else:
+            K, N, s, dt = 16, 3, 3, 0.01
+            g = dgsem.Grid(1, (K,), (0.0,), (1.0,), N, "advection", {"adv_vel": (1.0,)})
+            X = g.coordinates()
+            u = inputs.sine(X[0])
+            exact = lambda t: inputs.sine(X[0], t=t)
+        F = lambda x: dgsem.spatial_operator(g, x)
+        nslabs = job.get("nslabs", 1)
+        its = [0, 0]
+        for _ in range(nslabs):
+            if kind == "advection1d":
+                U, _ = ost.solve_slab_direct("stdg", F, u, dt, s)
+            else:
+                st = {}
+                U = ost.solve_slab_newton_gmres("stdg", F, u, dt, s, rtol=job["rtol"], maxit=30, gmres_m=30,
+                                                gmres_tol=job["eta"], gmres_maxit=2000, stats=st,
+                                                scaling="temporal_mass")
+                its[0] += st["newton_its"]
+                its[1] += st["gmres_its"]
+            u = U[s - 1]
+        out = {"oracle_s": time.perf_counter() - t_start, "dof_st": int(U.size), "oracle_newton_its": its[0],
+               "oracle_gmres_its": its[1], "rel_l2_vs_oracle": {}}
+        for name, ug in job["gpu"].items():
+            out["rel_l2_vs_oracle"][name] = _rel_lgl(g, ug.reshape(g.state_shape), u)
+        if exact is not None:
+            ue = exact(dt * nslabs)
+            out["oracle_rel_l2_nodal_vs_exact"] = float(np.linalg.norm(u - ue) / np.linalg.norm(ue))
+        return out
+    raise ValueError(kind)
+
+
+def _oracle_pool_map(jobs, workers):
+    """Run oracle jobs in `workers` spawned processes; results in job order."""
+    import concurrent.futures
+    import multiprocessing
+    _oracle_env()
+    ctx = multiprocessing.get_context("spawn")
+    with concurrent.futures.ProcessPoolExecutor(max_workers=max(1, workers), mp_context=ctx) as ex:
+        return list(ex.map(_oracle_job, jobs))
+
+
 def _default_dt():
     """dt of the workload, computed with the same CFL rule on the host (no GPU needed)."""
     import numpy as np
@@ -376,6 +521,13 @@ def gpu_arm(args):
         e2e_s = _max_over_ranks(time.perf_counter() - t0, ws)
         e2e_value = _sum_over_ranks(float(e2e_evals * dof), ws) / e2e_s / 1e9
         ctx.close()
+        # the first slabs of the same configuration from u0, for the oracle check (not timed)
+        with stdg.Context(desc, stream.cuda_stream) as cc:
+            cc.set_state(u0)
+            check_states = []
+            for _ in range(ORACLE_CHECK_SLABS):
+                cc.advance_slab()
+                check_states.append(cc.get_state())
 
         # ---- the same slabs on the mixed-precision path (FP32 exact Jv and Krylov basis,
         #      FP64 Newton residual and update): throughput and distance to the FP64 path
@@ -385,18 +537,20 @@ def gpu_arm(args):
         served = _serving_leg(stdg, [int(r) for r in args.serve_rates.split(",")], args.serve_requests) \
             if "serving" in args.legs and ws == 1 else None
         wave3d = _density_wave_leg(stdg, stream) if "wave3d" in args.legs and ws == 1 else None
+        adv1d = _advection_leg(stdg, stream) if "adv1d" in args.legs and ws == 1 else None
 
     lat_ms = sorted(1e3 * x for x in lat)
-    cpu = None
+    cpu, oracle_check = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # the CPU-baseline leg: the oracle timed on the host cores, and the error of every
+        # benchmarked GPU result against the oracle's solution from the same oracle runs
         try:
-            times, odof, oevals = run_oracle(1 + 20, dt)
-            T = sum(times[1:]) / len(times[1:])
-            cpu = {"value": oevals * odof / T / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": "20 x (1 FP64 residual + 1 complex-step Jv) of the full 64x64 N=4 s=4 slab "
-                             "(NumPy oracle, weak form, one thread) after one warm-up; %.1f s" % sum(times[1:])}
+            cpu, oracle_check = _cpu_baseline_leg(dt, check_states, batched, served, wave3d, adv1d)
         except Exception as e:  # report, do not hide
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: %s" % e}
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: %r" % e}
+    for leg in (batched, served, wave3d, adv1d):
+        if leg is not None:
+            leg.pop("_check", None)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
@@ -421,13 +575,82 @@ def gpu_arm(args):
                 "roofline": roofline, "clocks": clocks,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hin.numel() * 8),
                         "d2h_bytes_per_step": int(hout.numel() * 8)},
-                "gpu_launches": launches, "cpu_baseline": cpu, "mixed_fp32": mixed,
-                "batched": batched, "served": served, "density_wave_3d": wave3d}
+                "gpu_launches": launches, "cpu_baseline": cpu, "oracle_check": oracle_check,
+                "mixed_fp32": mixed, "batched": batched, "served": served, "density_wave_3d": wave3d,
+                "advection_1d": adv1d}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+ORACLE_CHECK_SLABS = 2      # headline slabs re-solved by the oracle
+ORACLE_SAMPLE = 16          # batched instances and served requests re-solved by the oracle
+ORACLE_MAX_DOF = 20000      # ... among those with at most this many space-time DOF (oracle time)
+SERVE_ORACLE_MAX_DOF = 120000
+CPU_REPS_1 = 60             # single-thread oracle sample: 60 x (residual + Jv) of the vortex slab
+CPU_REPS_ALL = 8            # all-core sample: every core runs 8 x (residual + Jv) concurrently
+
+
+def _cpu_baseline_leg(dt, check_states, batched, served, wave3d, adv1d):
+    """Oracle timings (one thread; all host cores as concurrent processes) and the oracle checks."""
+    import numpy as np
+    info = _cpu_info()
+    cores = max(1, info["usable"] or 1)
+    w = dict(WORKLOAD)
+    # (1) one thread
+    t0 = time.perf_counter()
+    one = _oracle_pool_map([{"kind": "eval_loop", "w": w, "dt": dt, "reps": 1 + CPU_REPS_1}], 1)[0]
+    t1 = time.perf_counter()
+    T1 = sum(one["times"][1:])
+    v1 = one["evals_per_rep"] * one["dof"] * CPU_REPS_1 / T1 / 1e9
+    # (2) every usable core: one process per core, each its own copy of the sample
+    allr = _oracle_pool_map([{"kind": "eval_loop", "w": w, "dt": dt, "reps": 1 + CPU_REPS_ALL}] * cores, cores)
+    v_all = sum(r["evals_per_rep"] * r["dof"] * CPU_REPS_ALL / sum(r["times"][1:]) for r in allr) / 1e9
+    # (3) oracle slab solves and the error of each benchmarked GPU result against them
+    jobs = [{"kind": "vortex_march", "w": w, "dt": dt, "gpu": check_states}]
+    names = ["headline"]
+    for leg, tag in ((batched, "batched"), (served, "served"), (wave3d, "density_wave_3d"),
+                     (adv1d, "advection_1d")):
+        for j in (leg or {}).get("_check", []):
+            jobs.append(j)
+            names.append(tag)
+    t2 = time.perf_counter()
+    res = _oracle_pool_map(jobs, min(cores, len(jobs)))
+    t3 = time.perf_counter()
+    check = {"tolerance_note": "relative LGL-weighted L2 distance of the GPU result to the oracle's FP64 slab "
+                               "solution of the same problem at the same Newton tolerance (each side stops at "
+                               "its own ||R|| <= rtol ||R(U0)||, so agreement is to the solve tolerance)",
+             "oracle_wall_s": t3 - t2}
+    head = res[0]["slabs"]
+    check["headline"] = {"slabs": head, "max_rel_l2_vs_oracle": max(x["rel_l2_vs_oracle"] for x in head)}
+    for tag in ("batched", "served", "density_wave_3d", "advection_1d"):
+        rs = [(j, r) for j, r, nm in zip(jobs, res, names) if nm == tag]
+        if not rs:
+            continue
+        errs = {}
+        for j, r in rs:
+            for k, e in r["rel_l2_vs_oracle"].items():
+                errs[k] = max(errs.get(k, 0.0), e)
+        entry = {"cases": [dict({kk: vv for kk, vv in j.items() if kk not in ("gpu", "kind")}, **r) for j, r in rs],
+                 "max_rel_l2_vs_oracle": errs}
+        check[tag] = entry
+    slab_times = [x["oracle_s"] for x in head]
+    cpu = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "%d x (1 FP64 residual + 1 complex-step Jv) of the full 64x64 N=4 s=4 vortex slab (NumPy "
+                     "oracle, weak form, one thread) after one warm-up; %.1f s" % (CPU_REPS_1, T1),
+           "cpu": info,
+           "all_cores": {"value": v_all, "unit": UNIT, "cores": cores,
+                         "sample": "%d processes (one per usable core), each %d x (residual + Jv) of its own copy "
+                                   "of the slab after one warm-up; summed throughput" % (cores, CPU_REPS_ALL)},
+           "oracle_slab_solve_s": {"per_slab": slab_times, "slabs_per_s": len(slab_times) / sum(slab_times),
+                                   "what": "the oracle's Newton-GMRES solve (left temporal-mass scaling, exact "
+                                           "complex-step Jv, one thread) of the first %d slabs of the headline "
+                                           "workload, run while other cores solved the other checks"
+                                           % len(slab_times)},
+           "single_thread_wall_s": t1 - t0}
+    return cpu, check
 
 
 def _mixed_path(stdg, desc, u0, args, stream, u_ref, ws):
@@ -585,8 +808,9 @@ def _batched_leg(stdg, stream, n_inst, n_seq, graphs=1):
         out_small = _run_batch(stdg, B, items[:n_seq])
         torch.cuda.synchronize()
         T_small = time.perf_counter() - t1
-    evals = sum((st["residual_evals"] + st["jv_evals"]) * dof for (_, st, _), (_, _, dof) in zip(out, items))
     statuses = [st for st, _, _ in out]
+    evals_ok = sum((st["residual_evals"] + st["jv_evals"]) * dof
+                   for (code, st, _), (_, _, dof) in zip(out, items) if code == 0)
     # sequential plain path on the first n_seq instances
     seq = []
     torch.cuda.synchronize()
@@ -601,23 +825,31 @@ def _batched_leg(stdg, stream, n_inst, n_seq, graphs=1):
     diffs = [float(np.linalg.norm(a[2] - b[1]) / np.linalg.norm(b[1])) for a, b in zip(out[:n_seq], seq)
              if a[0] == 0 and b[0] == 0]
     its = [st["gmres_its"] for _, st, _ in out]
+    # a seeded sample of instances small enough for the oracle, with their GPU results
+    import numpy as np
+    small = [i for i, it in enumerate(items) if it[2] <= ORACLE_MAX_DOF]
+    pick = sorted(np.random.default_rng(2201).choice(small, size=min(ORACLE_SAMPLE, len(small)), replace=False))
+    check = [{"kind": "burgers", "i": int(i), "rtol": WORK_TOL["newton_rtol"], "eta": WORK_TOL["gmres_rtol"],
+              "gpu_status": int(out[i][0]), "gpu": {"batched": out[i][2]}} for i in pick]
     vs_seq = None
     if n_seq > 0:
         vs_seq = {"instances": n_seq, "batched_s": T_small, "sequential_s": T_seq,
                   "batched_instances_per_s": n_seq / T_small, "sequential_instances_per_s": n_seq / T_seq,
                   "speedup": T_seq / T_small,
                   "max_rel_diff_to_sequential": max(diffs) if diffs else None,
+                  "pairs_compared": len(diffs), "pairs_not_converged": n_seq - len(diffs),
                   "sequential_path": "stdg_advance_slab per instance (context per instance), FP32 exact "
                                      "Jv + point-block preconditioner, restarted GMRES(30)"}
     return {"workload": "%d independent 2D viscous Burgers instances (seed 1000+i; side in {8,16,32,64}, N 2-6, "
                         "s 2-5, nu log-uniform [1e-3,1e-1]), one slab each, FP32 Krylov + FP64 Newton "
                         "refinement, Newton rtol 1e-10, FGMRES(30) rtol 1e-3" % n_inst,
             "instances": n_inst, "dof_total": int(sum(x[2] for x in items)), "arena_gb": arena / 1e9,
-            "slot_memory_gb": need / 1e9, "seconds": T, "instances_per_s": n_inst / T,
-            "gdof_evals_per_s": evals / T / 1e9,
+            "slot_memory_gb": need / 1e9, "seconds": T, "instances_per_s": statuses.count(0) / T,
+            "gdof_evals_per_s": evals_ok / T / 1e9, "failed": n_inst - statuses.count(0),
+            "counting": "instances_per_s and gdof_evals_per_s count the instances that converged (status 0)",
             "status_counts": {str(k): statuses.count(k) for k in sorted(set(statuses))},
             "gmres_its_mean": float(np.mean(its)), "gmres_its_max": int(max(its)),
-            "graphs": bool(graphs), "vs_sequential": vs_seq}
+            "graphs": bool(graphs), "vs_sequential": vs_seq, "_check": check}
 
 
 SERVE_SHARE_QUANTUM = 262144.0  # DOF: a request of L DOF advances every round(L / quantum)-th tick (<= 16)
@@ -625,6 +857,10 @@ SERVE_SHARE_MAX_STRIDE = 16
 
 
 def _serving_leg(stdg, rates, n_req):
+    """Served stream: n_req single-slab vortex requests per arrival rate, submitted on their Poisson
+    clock to a server; latency from submission to result.  The sequential baseline runs every
+    request alone through stdg_advance_slab (its service time measured on the GPU); its latencies
+    under the same arrivals are modelled from those service times with one FIFO queue."""
     import numpy as np
     import torch
     reqs = _vortex_requests(stdg, n_req)
@@ -635,7 +871,7 @@ def _serving_leg(stdg, rates, n_req):
                        "CFL 0.5, Newton rtol 1e-10, FGMRES(30) rtol 1e-3; Poisson arrivals (seed 7)",
            "requests_per_rate": n_req, "arena_gb": arena / 1e9, "rates": {}}
     # service times of the plain sequential GPU path (solve only, contexts created outside the timing)
-    svc, seq_status = [], []
+    svc, seq_status, seq_u = [], [], []
     stream = torch.cuda.Stream()
     for d, u0, _ in reqs:
         with stdg.Context(_sequential_config(stdg, d), stream.cuda_stream) as c:
@@ -645,8 +881,11 @@ def _serving_leg(stdg, rates, n_req):
             st = c.advance_slab(check=False)
             svc.append(time.perf_counter() - t0)
             seq_status.append(st["status"])
+            seq_u.append(c.get_state())
     runs = [(str(r), r, 0.0) for r in rates] + [("%d_shared" % rates[len(rates) // 2], rates[len(rates) // 2],
                                                     SERVE_SHARE_QUANTUM)]
+    first_res = None
+    pct = lambda v, q: 1e3 * v[min(len(v) - 1, int(q * len(v)))] if v else None
     for key, rate, quantum in runs:
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
         with stdg.Server(2, stdg.EULER, max(64, n_req), arena) as srv:
@@ -660,28 +899,41 @@ def _serving_leg(stdg, rates, n_req):
             res = [srv.poll(t, wait_s=600.0) for t in tickets]
             T = time.perf_counter() - t0
             cnt = srv.counters()
-        lat = sorted(r["latency_s"] for r in res)
-        # the sequential path under the same arrivals (one queue, measured service times)
+        if first_res is None:
+            first_res = res
+        ok = [r for r in res if r["status"] == 0]
+        lat = sorted(r["latency_s"] for r in ok)
+        # the sequential path under the same arrivals (one FIFO queue, measured service times)
         fin, seq_lat = 0.0, []
-        for ta, sv in zip(arrivals, svc):
+        for ta, sv, stt in zip(arrivals, svc, seq_status):
             fin = max(fin, ta) + sv
-            seq_lat.append(fin - ta)
+            if stt == 0:
+                seq_lat.append(fin - ta)
         seq_lat.sort()
-        pct = lambda v, q: 1e3 * v[min(len(v) - 1, int(q * len(v)))]
         out["rates"][key] = {
-            "served": {"p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "solves_per_s": n_req / T,
-                       "max_running": cnt["max_running"],
+            "served": {"p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "solves_per_s": len(ok) / T,
+                       "failed": n_req - len(ok), "max_running": cnt["max_running"],
+                       "arrivals_span_s": float(arrivals[-1]),
                        "statuses": {str(k): [r["status"] for r in res].count(k)
                                     for k in sorted({r["status"] for r in res})}},
-            "sequential": {"p50_ms": pct(seq_lat, 0.5), "p99_ms": pct(seq_lat, 0.99),
-                           "solves_per_s": n_req / fin}}
+            "sequential_modelled": {"p50_ms": pct(seq_lat, 0.5), "p99_ms": pct(seq_lat, 0.99),
+                                    "solves_per_s": len(seq_lat) / fin}}
     out["scheduling"] = {"graphs": True, "autotune": False,
                          "size_aware_sharing": "off, except the '<rate>_shared' run: a request of L DOF advances "
                                                "every round(L / %g)-th tick (at most %d)" %
                                                (SERVE_SHARE_QUANTUM, SERVE_SHARE_MAX_STRIDE)}
-    out["sequential_path"] = ("stdg_advance_slab per request in arrival order (FP32 exact Jv, point-block "
-                              "preconditioner); latencies from the measured service times under the same arrivals")
+    out["sequential_path"] = ("stdg_advance_slab per request (FP32 exact Jv, point-block preconditioner, "
+                              "restarted GMRES); service times measured on the GPU, latencies modelled from them "
+                              "under the same arrivals with one FIFO queue")
     out["sequential_statuses"] = {str(k): seq_status.count(k) for k in sorted(set(seq_status))}
+    out["counting"] = "solves_per_s and the latency percentiles count the requests that converged (status 0)"
+    # a seeded sample of requests small enough for the oracle, with the served and sequential results
+    small = [k for k, rq in enumerate(reqs) if rq[2] <= SERVE_ORACLE_MAX_DOF]
+    pick = sorted(np.random.default_rng(2202).choice(small, size=min(ORACLE_SAMPLE, len(small)), replace=False))
+    out["_check"] = [{"kind": "vortex_request", "side": int(reqs[k][0].cells[0]), "N": int(reqs[k][0].N),
+                      "s": int(reqs[k][0].s), "rtol": WORK_TOL["newton_rtol"], "eta": WORK_TOL["gmres_rtol"],
+                      "gpu_status": [int(first_res[k]["status"]), int(seq_status[k])],
+                      "gpu": {"served": first_res[k]["u"], "sequential": seq_u[k]}} for k in pick]
     return out
 
 
@@ -737,7 +989,68 @@ def _density_wave_leg(stdg, stream, slabs=2):
     out["rel_l2_mixed_vs_fp64"] = float(np.linalg.norm(finals["mixed_fp32"] - finals["fp64"]) /
                                         np.linalg.norm(finals["fp64"]))
     out["speedup_mixed"] = out["fp64"]["ms_per_slab"] / out["mixed_fp32"]["ms_per_slab"]
+    # the same configuration on a reduced grid (K^3, same N, s, CFL, tolerances, guess), both
+    # precisions, for the oracle check: the 32^3 grid is beyond the oracle's time budget
+    Kr = WAVE3D_CHECK_K
+    gpu = {}
+    for name, prec, jv in (("fp64", stdg.FP64, stdg.JV_FD), ("mixed_fp32", stdg.MIXED_FP32, stdg.JV_EXACT)):
+        dd = stdg.make_config(**dict(base, cells=[Kr, Kr, Kr], dt=1.0, precision=prec, jv_mode=jv))
+        with stdg.Context(dd, stream.cuda_stream) as c:
+            Xr = c.node_coordinates()
+        ur = np.ascontiguousarray(inputs.density_wave(Xr[:, 0], Xr[:, 1], Xr[:, 2]).ravel())
+        q = ur.reshape(-1, 5)
+        pr = 0.4 * (q[:, 4] - 0.5 * (q[:, 1] ** 2 + q[:, 2] ** 2 + q[:, 3] ** 2) / q[:, 0])
+        dtr = 0.5 * (1.0 / Kr) / float(np.max(np.abs(q[:, 1] / q[:, 0]) + np.sqrt(1.4 * pr / q[:, 0])))
+        with stdg.Context(stdg.make_config(**dict(base, cells=[Kr, Kr, Kr], dt=dtr, precision=prec, jv_mode=jv)),
+                          stream.cuda_stream) as c:
+            c.set_state(ur)
+            for _ in range(WAVE3D_CHECK_SLABS):
+                c.advance_slab()
+            gpu[name] = c.get_state()
+    out["_check"] = [{"kind": "wave3d", "K": Kr, "N": N, "s": s, "nslabs": WAVE3D_CHECK_SLABS,
+                      "rtol": base["newton_rtol"], "eta": base["gmres_rtol"], "gpu": gpu}]
     return out
+
+
+WAVE3D_CHECK_K = 4
+WAVE3D_CHECK_SLABS = 2
+
+
+def _advection_leg(stdg, stream, slabs=100, reps=5):
+    """1D linear advection u_t + u_x = 0 on the periodic unit interval: 16 elements, N = 3, s = 3,
+    dt = 0.01, 100 slabs from u0 = sin(2 pi x) (192 space-time DOF per slab).  Launch-latency bound:
+    reported as microseconds per slab (CUDA events around each 100-slab march; best and median of
+    `reps` marches) and compared with the oracle's march."""
+    import numpy as np
+    import torch
+    from paper_2201_05800_gb300 import inputs
+    d = stdg.make_config(dim=1, cells=[16, 1, 1], lo=[0, 0, 0], hi=[1, 1, 1], N=3, s=3, equation=stdg.ADVECTION,
+                         adv_vel=[1.0, 0.0, 0.0], dt=0.01, newton_rtol=1e-10, gmres_m=30, gmres_rtol=1e-3)
+    with stdg.Context(d, stream.cuda_stream) as c:
+        X = c.node_coordinates()
+        u0 = np.ascontiguousarray(inputs.sine(X[:, 0]).ravel())
+        ms = []
+        for _ in range(reps + 1):
+            c.set_state(u0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            st = [c.advance_slab() for _ in range(slabs)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        u = c.get_state()
+        launches = sum(p["launches"] for p in c.profile_read(reset=True).values())
+    ms = ms[1:]
+    exact = inputs.sine(X[:, 0], t=slabs * 0.01).ravel()
+    return {"workload": "1D linear advection, 16 elements on [0,1], N=3, s=3, dt=0.01, u0=sin(2 pi x), "
+                        "%d slabs, Newton rtol 1e-10, GMRES(30) rtol 1e-3, FP64" % slabs,
+            "dof_st": 192, "us_per_slab_best": 1e3 * min(ms) / slabs,
+            "us_per_slab_median": 1e3 * sorted(ms)[len(ms) // 2] / slabs,
+            "newton_its_last": st[-1]["newton_its"], "gmres_its_last": st[-1]["gmres_its"],
+            "launches_per_slab": launches / ((reps + 1) * slabs),
+            "rel_l2_nodal_vs_exact": float(np.linalg.norm(u - exact) / np.linalg.norm(exact)),
+            "_check": [{"kind": "advection1d", "nslabs": slabs, "gpu": {"fp64": u}}]}
 
 
 def _ncu_traffic():
@@ -761,8 +1074,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="mixed,batched,serving,wave3d",
-                    help="extra legs after the main FP64 line: mixed,batched,serving,wave3d (or none)")
+    ap.add_argument("--legs", default="mixed,batched,serving,wave3d,adv1d",
+                    help="extra legs after the main FP64 line: mixed,batched,serving,wave3d,adv1d (or none)")
     ap.add_argument("--batch-instances", type=int, default=4096)
     ap.add_argument("--batch-sequential", type=int, default=48,
                     help="instances solved one at a time for the batched-vs-sequential comparison")
