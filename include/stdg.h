@@ -392,6 +392,18 @@ stdg_status stdg_server_set_queue_limit(stdg_server* s, size_t max_queued);
 /* The batch knobs of stdg_batch_configure, applied before the worker's next round. */
 stdg_status stdg_server_configure(stdg_server* s, double share_quantum, int share_max_stride, int use_graphs,
                                   int autotune);
+/* Admission policy, applied from the worker's next admission round.
+ *   order 0: arrival order (the head of the queue blocks the ones behind it);
+ *   order 1: the queued request with the fewest space-time DOF first (ties in
+ *            arrival order): short requests do not wait behind long ones;
+ *   max_running_dof > 0: no request is admitted while the admitted ones
+ *            already hold that many space-time DOF (a larger request is
+ *            admitted when nothing runs), so that each tick stays short;
+ *            0: admission by device memory only.
+ * Defaults: 0, 0.  A request's result does not depend on the policy (slots
+ * are independent).  STDG_ERR_INVALID_ARG for an unknown order or a negative
+ * or NaN cap. */
+stdg_status stdg_server_set_policy(stdg_server* s, int order, double max_running_dof);
 /* Counters since creation; returns the worker's fatal status (STDG_OK if none). */
 stdg_status stdg_server_counters(stdg_server* s, unsigned long long* admitted, unsigned long long* completed,
                                  unsigned long long* ticks, int* queued, int* running, int* max_running);
@@ -410,6 +422,20 @@ stdg_status stdg_lgl_constants(int n, double* x, double* w, double* D);
  * E[m*s + j] = l_j(tau_m + 2) for the s-point temporal LGL rule, 2 <= s <= 5
  * (s*s doubles written to E, caller-owned).  STDG_ERR_INVALID_ARG otherwise. */
 stdg_status stdg_predictor_matrix(int s, double* E);
+/* Spectral data of the batch engine's global preconditioner (host only, no GPU
+ * needed; no counterpart in the paper, which uses SOR on an assembled
+ * Jacobian).  The periodic 1D operator A of K elements of width h (N+1 LGL
+ * nodes): the symmetric interior penalty form of -nu d^2/dx^2 (Sec. 3.1, penalty
+ * eta, eta <= 0 meaning 10 N^2, h_e = h) plus the upwind dissipation lam/2 [[u]]
+ * of the Rusanov flux (Eq. flux:llf) with the constant speed lam.  Its
+ * eigenvectors are phi[e][i] = exp(2 pi i k e / K) V_k[i][j], k < K, j <= N:
+ * lambda[k (N+1) + j] receives the eigenvalue, Vre / Vim[(k (N+1) + i)(N+1) + j]
+ * the real and imaginary parts of V_k[i][j] (caller-owned arrays of K (N+1) and
+ * K (N+1)^2 doubles).  STDG_ERR_INVALID_ARG for N outside 1..7, K < 1, h <= 0,
+ * nu < 0, lam < 0 or a NULL pointer; STDG_ERR_NOT_CONVERGED if an eigensolve
+ * did not converge. */
+stdg_status stdg_fdm_symbol(int N, int K, double h, double nu, double eta, double lam, double* lambda,
+                            double* Vre, double* Vim);
 
 #ifdef __cplusplus
 }

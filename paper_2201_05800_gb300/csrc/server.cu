@@ -45,6 +45,8 @@ size_t state_len(const stdg_config_desc& d) {
   return n;
 }
 
+double slab_dof(const stdg_config_desc& d) { return (double)state_len(d) * d.s; }
+
 }  // namespace
 
 struct stdg_server {
@@ -71,6 +73,12 @@ struct stdg_server {
   double share_quantum = 0.0;
   int share_max_stride = 16, use_graphs = 1, autotune = 0;
   size_t max_queue = 0;                          // 0: unbounded submission queue
+  // admission policy (stdg_server_set_policy): order 0 = arrival (FIFO), 1 = smallest space-time
+  // problem first (ties in arrival order); max_running_dof > 0 caps the space-time DOF admitted
+  // at once (a request larger than the cap runs alone)
+  int order = 0;
+  double max_running_dof = 0.0;
+  double running_dof = 0.0;
   std::vector<int> cancel_slots;                 // slots of cancelled requests, released by the worker
 };
 
@@ -122,8 +130,16 @@ void worker_main(stdg_server* s) {
         s->cv.wait_for(lk, std::chrono::milliseconds(50), [&] { return s->stop || !s->queue.empty(); });
       if (s->stop) break;
       while (!s->queue.empty()) {
-        const unsigned long long t = s->queue.front();
+        // next candidate: the head of the queue, or its smallest problem
+        auto pick = s->queue.begin();
+        if (s->order == 1) {
+          for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+            if (slab_dof(s->reqs[*it].d) < slab_dof(s->reqs[*pick].d)) pick = it;
+        }
+        const unsigned long long t = *pick;
         Request& r = s->reqs[t];
+        const double dof = slab_dof(r.d);
+        if (s->max_running_dof > 0.0 && !s->running.empty() && s->running_dof + dof > s->max_running_dof) break;
         int slot = -1;
         const stdg_status as = stdg_batch_add(s->batch, &r.d, r.u.data(), STDG_HOST, &slot);
         if (as == STDG_ERR_OOM) {
@@ -131,13 +147,13 @@ void worker_main(stdg_server* s) {
             r.done = true;
             r.status = STDG_ERR_OOM;
             r.t_admit = r.t_done = Clock::now();
-            s->queue.pop_front();
+            s->queue.erase(pick);
             s->cv.notify_all();
             continue;
           }
           break;
         }
-        s->queue.pop_front();
+        s->queue.erase(pick);
         if (as != STDG_OK) {
           r.done = true;
           r.status = as;
@@ -148,6 +164,7 @@ void worker_main(stdg_server* s) {
         r.slot = slot;
         r.t_admit = Clock::now();
         s->running[slot] = t;
+        s->running_dof += dof;
         ++s->n_admitted;
       }
       if ((int)s->running.size() > s->max_running) s->max_running = (int)s->running.size();
@@ -195,6 +212,7 @@ void worker_main(stdg_server* s) {
       if (it == s->reqs.end() || it->second.done || s->running.count(sr.first) == 0) continue;  // cancelled meanwhile
       stdg_batch_remove(s->batch, sr.first);
       Request& r = it->second;
+      s->running_dof -= slab_dof(r.d);
       r.slot = -1;
       r.u.swap(out);
       r.status = gs == STDG_OK ? status : gs;
@@ -309,6 +327,7 @@ stdg_status stdg_server_cancel(stdg_server* s, unsigned long long ticket) {
     s->queue.erase(q);
   } else if (r.slot >= 0) {
     s->running.erase(r.slot);
+    s->running_dof -= slab_dof(r.d);
     s->cancel_slots.push_back(r.slot);
     r.slot = -1;
   }
@@ -336,6 +355,14 @@ stdg_status stdg_server_configure(stdg_server* s, double share_quantum, int shar
   s->use_graphs = use_graphs;
   s->autotune = autotune;
   s->cfg_dirty = true;
+  return STDG_OK;
+}
+
+stdg_status stdg_server_set_policy(stdg_server* s, int order, double max_running_dof) {
+  if (!s || (order != 0 && order != 1) || !(max_running_dof >= 0.0)) return STDG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->order = order;
+  s->max_running_dof = max_running_dof;
   return STDG_OK;
 }
 

@@ -92,6 +92,8 @@ _SIGS = {
     "stdg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "stdg_version": (ctypes.c_char_p, []),
     "stdg_predictor_matrix": (ctypes.c_int, [ctypes.c_int, _P]),
+    "stdg_fdm_symbol": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, _P, _P, _P]),
     "stdg_lgl_constants": (ctypes.c_int, [ctypes.c_int, _P, _P, _P]),
 }
 
@@ -329,6 +331,7 @@ _BATCH_SIGS.update({
     "stdg_batch_configure": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "stdg_server_configure": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "stdg_server_cancel": (ctypes.c_int, [_P, ctypes.c_ulonglong]),
+    "stdg_server_set_policy": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
     "stdg_server_set_queue_limit": (ctypes.c_int, [_P, ctypes.c_size_t]),
     "stdg_server_create": (ctypes.c_int, [ctypes.POINTER(stdg_batch_desc), ctypes.c_int, ctypes.POINTER(_P)]),
     "stdg_server_destroy": (ctypes.c_int, [_P]),
@@ -528,6 +531,12 @@ class Server:
         if st != 0:
             raise StdgError(st, "stdg_server_configure failed")
 
+    def set_policy(self, order=0, max_running_dof=0.0):
+        """stdg_server_set_policy: 0 = arrival order, 1 = smallest first; cap on admitted DOF."""
+        st = self._lib.stdg_server_set_policy(self._h, int(order), float(max_running_dof))
+        if st != 0:
+            raise StdgError(st, "stdg_server_set_policy failed")
+
     def cancel(self, ticket):
         st = self._lib.stdg_server_cancel(self._h, ticket)
         if st != 0:
@@ -563,6 +572,18 @@ def lgl_constants(n):
     if st != 0:
         raise StdgError(st, status_string(st))
     return x, w, D
+
+
+def fdm_symbol(N, K, h, nu, eta, lam):
+    """stdg_fdm_symbol: eigenvalues (K, N+1) and eigenvector blocks V (K, N+1, N+1) of the periodic
+    1D operator the batch engine's global preconditioner diagonalises."""
+    n = N + 1
+    lam_out = np.empty(K * n)
+    vre, vim = np.empty(K * n * n), np.empty(K * n * n)
+    st = load().stdg_fdm_symbol(N, K, h, nu, eta, lam, lam_out.ctypes.data, vre.ctypes.data, vim.ctypes.data)
+    if st != 0:
+        raise StdgError(st, "stdg_fdm_symbol failed")
+    return lam_out.reshape(K, n), (vre + 1j * vim).reshape(K, n, n)
 
 
 def predictor_matrix(s):

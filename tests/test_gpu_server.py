@@ -141,3 +141,31 @@ def test_cancel_queued_and_running_requests(S):
         assert np.array_equal(results[0]["u"], u_alone)
     for r in (results[1], results[3]):
         assert r["status"] == 0 and np.array_equal(r["u"], u_alone)
+
+
+@pytest.mark.parametrize("order,cap", [(1, 0.0), (1, 3000.0), (0, 3000.0)])
+def test_admission_policy_keeps_results(S, order, cap):
+    """Smallest-first admission and a cap on the admitted space-time DOF change only when a
+    request runs: every result stays bitwise the one it has alone.  With the cap, the DOF held
+    by the admitted requests never exceeds it (a larger request runs alone)."""
+    reqs = _requests(8, seed=5)
+    with S.Server(2, S.EULER, 16, 512 << 20) as srv:
+        srv.set_policy(order, cap)
+        tickets = [srv.submit(p.config(**WORK), u0) for p, u0 in reqs]
+        results = [srv.poll(t, wait_s=120.0) for t in tickets]
+        counters = srv.counters()
+    assert counters["fatal"] == 0 and counters["completed"] == len(reqs)
+    if cap:
+        dof = np.cumsum(sorted(u0.size * p.s for p, u0 in reqs))
+        assert counters["max_running"] <= max(1, int(np.sum(dof <= cap)))
+    for (p, u0), r in zip(reqs, results):
+        assert r is not None and r["status"] == 0, r
+        u_alone, (done, status, st) = _alone(S, p, u0)
+        assert np.array_equal(r["u"], u_alone) and r["stats"] == st
+
+
+def test_admission_policy_rejects_bad_arguments(S):
+    with S.Server(2, S.EULER, 4, 64 << 20) as srv:
+        for order, cap in ((2, 0.0), (-1, 0.0), (0, -1.0), (0, float("nan"))):
+            with pytest.raises(S.StdgError):
+                srv.set_policy(order, cap)
