@@ -283,15 +283,21 @@ stdg_status stdg_slab_norm_noalloc(const double* x, size_t len, double* out, voi
  *   Newton on R(U) = 0 from U0 = 1 (x) u^n, FP64 residual and update
  *   (stop: ||R||_2 <= max(newton_rtol ||R(U0)||_2, newton_atol)), each step
  *   solving J dU = -R by flexible GMRES(gmres_m) (no restart; the step takes
- *   the iterate after at most gmres_m iterations or at gmres_rtol), right-
+ *   the iterate after at most gmres_m iterations or at gmres_rtol; at most
+ *   newton_maxit x ceil(gmres_maxit / gmres_m) such steps, the GMRES-iteration
+ *   budget of the single-slab solver), right-
  *   preconditioned, with FP32 Krylov vectors and exact (forward-mode) FP32
  *   Jacobian-vector products; then u^{n+1} = U^s.  Preconditioner: Euler and
  *   inst->precond == STDG_PRECOND_POINT_BLOCK: the point-block P above;
- *   otherwise (scalar equations) an element tensor-product inverse: the
- *   temporal block together with the element-local interior penalty operator
- *   and an upwind face dissipation with the slot's wave-speed bound (|a| for
- *   advection, max |u0| for Burgers), applied exactly by fast diagonalisation
- *   (1D eigenvectors along each direction, an s x s inverse per mode).
+ *   scalar equations on grids whose element counts are powers of two (and
+ *   whose lines fit 4096 values): the global inverse of
+ *   C (x) I - dt/2 M_tau (x) (A_x (+) A_y), A_a the periodic 1D operator of the
+ *   interior penalty form plus an upwind face dissipation with the slot's
+ *   wave-speed bound (|a| for advection, max |u0| for Burgers), applied
+ *   exactly by fast diagonalisation (FFT over the elements and per-mode
+ *   eigenvectors along each direction, an s x s solve per spatial mode; see
+ *   stdg_fdm_symbol); other scalar slots: the same with the element-local
+ *   operator (neighbours set to zero) in place of A_a.
  * A slot's result does not depend on the other slots (no reduction crosses
  * slots, all reductions have a fixed order): bitwise the same alone or in a
  * mix.  Slot memory comes from one device arena of hbm_budget_bytes
@@ -311,9 +317,10 @@ stdg_status stdg_batch_destroy(stdg_batch* b);
 /* Admit one slab problem with initial state u0 (state layout, stdg_state_len
  * values of the problem, host or device pointer).  inst->dim and
  * inst->equation must match the batch; inst->gmres_m (1..31),
- * newton_rtol/atol/maxit and gmres_rtol are used; precision, jv_mode, precond,
- * predictor (a slot solves one slab from 1 (x) u0) and gmres_maxit are ignored
- * (see above).  *slot receives the slot id.
+ * newton_rtol/atol/maxit, gmres_rtol and gmres_maxit are used; precision,
+ * jv_mode, precond (but for STDG_PRECOND_POINT_BLOCK on scalar equations) and
+ * predictor (a slot solves one slab from 1 (x) u0) are ignored (see above).
+ * *slot receives the slot id.
  * STDG_ERR_OOM: the arena (or the slot table) is full; nothing changed. */
 stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* inst, const double* u0, int ptr_kind, int* slot);
 /* Run `ticks` ticks (>= 1), then report in *working how many admitted slots

@@ -11,6 +11,7 @@
 #include "args_host.cuh"
 #include "lgl_host.h"
 #include "engine.cuh"
+#include "fdm_host.h"
 #include "engine_ops.cuh"
 #include "ops.h"
 #include "stdg.h"
@@ -22,6 +23,7 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int kChunkValues = 16384;   // values per work item of the build / dot / update kernels
 constexpr size_t kOpSmemCap = 96 * 1024;
+constexpr size_t kFdmMaxLine = 4096;  // complex values of one x-line group or one y column of the fdm passes
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -75,6 +77,10 @@ struct Layout {
   long long nelem;
   size_t L, S, npinv;
   size_t off_U, off_R, off_uprev, off_U32, off_Pinv, off_V, off_Z, off_K, kfloats, bytes;
+  // global fast-diagonalisation preconditioner (fdm): eligibility, FFT sizes, data and scratch
+  int fdm, kx, ky, ny, logx, logy;
+  int f_twx, f_Fx, f_Bx, f_lx, f_twy, f_Fy, f_By, f_ly;
+  size_t off_F, ffloats, off_X;
 };
 
 struct HostSlot {
@@ -100,7 +106,13 @@ struct stdg_batch {
   OpArgs<double>* a64 = nullptr;
   OpArgs<float>* a32 = nullptr;
   SlotBuf* buf = nullptr;
-  int* counts = nullptr;  // [0] op items, [1] chunk items
+  int* counts = nullptr;  // [0] op items, [1] chunk items, [2] fdm row items, [3] fdm column items
+  EngItem* fdm_rows = nullptr;
+  EngItem* fdm_cols = nullptr;
+  size_t cap_frows = 0, cap_fcols = 0;
+  int n_frows = 0, n_fcols = 0;
+  bool any_fdm = false;
+  size_t fdm_smem[3] = {0, 0, 0};
   int* active_d = nullptr;
   int* phase_d = nullptr;
   EngItem* op_items = nullptr;
@@ -222,6 +234,39 @@ Layout layout_of(const stdg_config_desc* d) {
   l.off_K = o;
   l.kfloats = (size_t)4 * l.n * l.n + (size_t)l.nd * l.s * l.s;
   o += align_up(l.kfloats * 4);
+  // global preconditioner of scalar slots (not with the point-block option): element counts that
+  // are powers of two (radix-2 FFT) and lines that fit the shared-memory tiles of its kernels
+  l.fdm = 0;
+  l.ffloats = 0;
+  l.off_F = l.off_X = o;
+  const int kx = d->cells[0], ky = d->dim > 1 ? d->cells[1] : 1;
+  auto pow2 = [](int k) { return k >= 1 && (k & (k - 1)) == 0; };
+  l.ny = d->dim > 1 ? l.n : 1;
+  if (d->equation != STDG_EULER && d->precond != STDG_PRECOND_POINT_BLOCK && d->dim <= 2 && pow2(kx) && pow2(ky) &&
+      (size_t)kx * l.n * l.ny <= kFdmMaxLine && (size_t)l.s * ky * l.ny <= kFdmMaxLine) {
+    l.fdm = 1;
+    l.kx = kx;
+    l.ky = ky;
+    l.logx = 0;
+    while ((1 << l.logx) < kx) ++l.logx;
+    l.logy = 0;
+    while ((1 << l.logy) < ky) ++l.logy;
+    auto even = [](size_t v) { return (int)((v + 1) & ~(size_t)1); };  // complex data on 8-byte boundaries
+    int f = 0;
+    l.f_twx = f; f += even(2 * kx);
+    l.f_Fx = f;  f += even(2 * (size_t)kx * l.n * l.n);
+    l.f_Bx = f;  f += even(2 * (size_t)kx * l.n * l.n);
+    l.f_lx = f;  f += even((size_t)kx * l.n);
+    l.f_twy = f; f += even(2 * ky);
+    l.f_Fy = f;  f += even(2 * (size_t)ky * l.ny * l.ny);
+    l.f_By = f;  f += even(2 * (size_t)ky * l.ny * l.ny);
+    l.f_ly = f;  f += even((size_t)ky * l.ny);
+    l.ffloats = f;
+    l.off_F = o;
+    o += align_up(l.ffloats * 4);
+    l.off_X = o;
+    o += align_up(l.L * 8);  // one complex value per slab value
+  }
   l.bytes = o;
   return l;
 }
@@ -264,8 +309,10 @@ cudaError_t probe(const stdg_batch* b, int mode, const OpArgs<double>& a64, cons
 
 // Work-item lists and slot records of the active slots.
 stdg_status rebuild(stdg_batch* b) {
-  std::vector<EngItem> op, ch;
+  std::vector<EngItem> op, ch, frows, fcols;
   b->smem64 = b->smem32 = 0;
+  b->any_fdm = false;
+  b->fdm_smem[0] = b->fdm_smem[1] = b->fdm_smem[2] = 0;
   b->any_kron = false;
   for (int id : b->active) b->any_kron = b->any_kron || b->slots[id].buf.kron;
   for (int id : b->active) {
@@ -277,6 +324,15 @@ stdg_status rebuild(stdg_batch* b) {
     for (long long t = 0; t < std::max(tiles, tiles32); ++t) op.push_back({id, (int)t});
     hs.buf.item0 = (int)ch.size();
     for (int c = 0; c < hs.buf.nitems; ++c) ch.push_back({id, c});
+    if (hs.buf.fdm) {
+      b->any_fdm = true;
+      for (int r = 0; r < l.ky * l.s; ++r) frows.push_back({id, r});
+      for (int r = 0; r < l.kx * l.n; ++r) fcols.push_back({id, r});
+      const size_t line = (size_t)l.kx * l.n * l.ny, col = (size_t)l.s * l.ky * l.ny;
+      b->fdm_smem[0] = std::max(b->fdm_smem[0], line * sizeof(float2));
+      b->fdm_smem[1] = std::max(b->fdm_smem[1], 2 * col * sizeof(float2));
+      b->fdm_smem[2] = std::max(b->fdm_smem[2], 2 * line * sizeof(float2));
+    }
     b->smem64 = std::max(b->smem64, operator_smem_bytes(l.dim, l.r, 8, kModeResidual, l.n, l.s, hs.epb64));
     b->smem32 = std::max(b->smem32, operator_smem_bytes(l.dim, l.r, 4, kModeJvExact, l.n, l.s, hs.epb32));
     BCK(b, cudaMemcpyAsync(b->buf + id, &hs.buf, sizeof(SlotBuf), cudaMemcpyHostToDevice, b->st));
@@ -310,7 +366,13 @@ stdg_status rebuild(stdg_batch* b) {
     BCK(b, cudaMemcpyAsync(b->op_items, op.data(), op.size() * sizeof(EngItem), cudaMemcpyHostToDevice, b->st));
   if (!ch.empty())
     BCK(b, cudaMemcpyAsync(b->chunk_items, ch.data(), ch.size() * sizeof(EngItem), cudaMemcpyHostToDevice, b->st));
-  int cnt[2] = {(int)op.size(), (int)ch.size()};
+  BCK(b, grow(&b->fdm_rows, &b->cap_frows, std::max<size_t>(frows.size(), 1), b->st));
+  BCK(b, grow(&b->fdm_cols, &b->cap_fcols, std::max<size_t>(fcols.size(), 1), b->st));
+  if (!frows.empty())
+    BCK(b, cudaMemcpyAsync(b->fdm_rows, frows.data(), frows.size() * sizeof(EngItem), cudaMemcpyHostToDevice, b->st));
+  if (!fcols.empty())
+    BCK(b, cudaMemcpyAsync(b->fdm_cols, fcols.data(), fcols.size() * sizeof(EngItem), cudaMemcpyHostToDevice, b->st));
+  int cnt[4] = {(int)op.size(), (int)ch.size(), (int)frows.size(), (int)fcols.size()};
   BCK(b, cudaMemcpyAsync(b->counts, cnt, sizeof(cnt), cudaMemcpyHostToDevice, b->st));
   if (!b->active.empty())
     BCK(b, cudaMemcpyAsync(b->active_d, b->active.data(), b->active.size() * sizeof(int), cudaMemcpyHostToDevice,
@@ -321,11 +383,19 @@ stdg_status rebuild(stdg_batch* b) {
     L.op_smem64 = b->smem64;
     L.op_smem32 = b->smem32;
     BCK(b, physics(b, L, 1));
+    if (b->any_fdm) {
+      L.fdm_smem_a = b->fdm_smem[0];
+      L.fdm_smem_b = b->fdm_smem[1];
+      L.fdm_smem_c = b->fdm_smem[2];
+      BCK(b, eng_fdm_prepare(L));
+    }
   }
   // the host vectors are pageable: make the copies complete before they go out of scope
   BCK(b, cudaStreamSynchronize(b->st));
   b->n_op = cnt[0];
   b->n_chunk = cnt[1];
+  b->n_frows = cnt[2];
+  b->n_fcols = cnt[3];
   b->dirty = false;
   return STDG_OK;
 }
@@ -353,6 +423,16 @@ stdg_status tick(stdg_batch* b) {
   L.partials = b->partials;
   L.tick = b->tick_d;
   L.any_kron = b->any_kron ? 1 : 0;
+  L.fdm_rows = b->fdm_rows;
+  L.n_fdm_rows = b->counts + 2;
+  L.fdm_cols = b->fdm_cols;
+  L.n_fdm_cols = b->counts + 3;
+  L.any_fdm = b->any_fdm ? 1 : 0;
+  L.fdm_grid_rows = std::max(1, std::min(b->n_frows, b->sms * 4));
+  L.fdm_grid_cols = std::max(1, std::min(b->n_fcols, b->sms * 4));
+  L.fdm_smem_a = b->fdm_smem[0];
+  L.fdm_smem_b = b->fdm_smem[1];
+  L.fdm_smem_c = b->fdm_smem[2];
   cudaError_t e = physics(b, L, 0);
   if (e != cudaSuccess) return bfail(b, STDG_ERR_CUDA, std::string("engine physics launch: ") + cudaGetErrorString(e));
   e = eng_tick_tail(L, b->st);
@@ -529,6 +609,45 @@ std::vector<float> kron_data(const stdg_config_desc* d, int n, int s, int nd, co
   return out;
 }
 
+// Data of the global fast-diagonalisation preconditioner of a scalar slot (see engine_fdm.cu):
+// twiddles exp(-2 pi i t / K), the per-mode transforms F_k, B_k and eigenvalues of the periodic
+// 1D operator along x and y (fdm_host.h), as FP32 at the offsets of the layout.
+bool fdm_data(const stdg_config_desc* d, const Layout& l, const double lam[3], std::vector<float>* out) {
+  out->assign(l.ffloats, 0.0f);
+  float* o = out->data();
+  const double pi = 3.14159265358979323846;
+  double xi[16], w[16];
+  lgl_rule(l.n, xi, w);
+  const int dims[2] = {l.kx, l.ky};
+  const int offs[2][4] = {{l.f_twx, l.f_Fx, l.f_Bx, l.f_lx}, {l.f_twy, l.f_Fy, l.f_By, l.f_ly}};
+  for (int a = 0; a < 2; ++a) {
+    const int K = dims[a];
+    for (int t = 0; t < K; ++t) {
+      o[offs[a][0] + 2 * t] = (float)std::cos(2.0 * pi * t / K);
+      o[offs[a][0] + 2 * t + 1] = (float)-std::sin(2.0 * pi * t / K);
+    }
+    if (a == 1 && d->dim == 1) {  // no y direction: identity transforms, eigenvalue 0
+      o[offs[a][1]] = o[offs[a][2]] = 1.0f;
+      o[offs[a][3]] = 0.0f;
+      continue;
+    }
+    const int n = l.n;
+    const double h = (d->hi[a] - d->lo[a]) / d->cells[a];
+    std::vector<double> A0(n * n), Ap(n * n), Am(n * n), lmb((size_t)K * n);
+    std::vector<cplx> B((size_t)K * n * n), F((size_t)K * n * n);
+    fdm_blocks_1d(n, h, d->viscosity, d->penalty, lam[a], A0.data(), Ap.data(), Am.data());
+    if (!fdm_symbol_eig(n, K, A0.data(), Ap.data(), Am.data(), w, lmb.data(), B.data(), F.data())) return false;
+    for (size_t i = 0; i < B.size(); ++i) {
+      o[offs[a][1] + 2 * i] = (float)F[i].real();
+      o[offs[a][1] + 2 * i + 1] = (float)F[i].imag();
+      o[offs[a][2] + 2 * i] = (float)B[i].real();
+      o[offs[a][2] + 2 * i + 1] = (float)B[i].imag();
+    }
+    for (size_t i = 0; i < lmb.size(); ++i) o[offs[a][3] + i] = (float)lmb[i];
+  }
+  return true;
+}
+
 // Elements per CTA of the two op kernels for the slot's class: cached, else measured.  The
 // probe is a virtual periodic grid of the class with at least 4096 elements (enough CTAs to
 // fill the GPU, as in a loaded batch) holding a uniform state; each candidate tile is timed
@@ -663,7 +782,7 @@ stdg_status stdg_batch_create(const stdg_batch_desc* desc, void* cuda_stream, st
   ok = ok && cudaMalloc(&b->a64, ns * sizeof(OpArgs<double>)) == cudaSuccess;
   ok = ok && cudaMalloc(&b->a32, ns * sizeof(OpArgs<float>)) == cudaSuccess;
   ok = ok && cudaMalloc(&b->buf, ns * sizeof(SlotBuf)) == cudaSuccess;
-  ok = ok && cudaMalloc(&b->counts, 2 * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->counts, 4 * sizeof(int)) == cudaSuccess;
   ok = ok && cudaMalloc(&b->active_d, ns * sizeof(int)) == cudaSuccess;
   ok = ok && cudaMalloc(&b->phase_d, ns * sizeof(int)) == cudaSuccess;
   ok = ok && cudaMallocHost(&b->phase_h, ns * sizeof(int)) == cudaSuccess;
@@ -674,7 +793,7 @@ stdg_status stdg_batch_create(const stdg_batch_desc* desc, void* cuda_stream, st
     return STDG_ERR_OOM;
   }
   if (cudaMemsetAsync(b->ctl, 0, ns * sizeof(SlotCtl), b->st) != cudaSuccess ||
-      cudaMemsetAsync(b->counts, 0, 2 * sizeof(int), b->st) != cudaSuccess ||
+      cudaMemsetAsync(b->counts, 0, 4 * sizeof(int), b->st) != cudaSuccess ||
       cudaMemsetAsync(b->tick_d, 0, sizeof(int), b->st) != cudaSuccess ||
       cudaStreamSynchronize(b->st) != cudaSuccess) {
     cudaGetLastError();
@@ -692,7 +811,7 @@ stdg_status stdg_batch_destroy(stdg_batch* b) {
   cudaStreamSynchronize(b->st);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   void* ps[] = {b->arena_base, b->ctl, b->a64, b->a32, b->buf, b->counts, b->active_d, b->phase_d,
-                b->op_items, b->chunk_items, b->partials, b->tick_d};
+                b->op_items, b->chunk_items, b->partials, b->tick_d, b->fdm_rows, b->fdm_cols};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (b->phase_h) cudaFreeHost(b->phase_h);
@@ -755,6 +874,22 @@ stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* d, const doubl
   sb.n = l.n;
   sb.kron = (d->equation != STDG_EULER && d->precond != STDG_PRECOND_POINT_BLOCK) ? 1 : 0;
   sb.kdat = reinterpret_cast<const float*>(base + l.off_K);
+  sb.fdm = 0;
+  sb.fkx = l.kx;
+  sb.fky = l.ky;
+  sb.fny = l.ny;
+  sb.flogx = l.logx;
+  sb.flogy = l.logy;
+  sb.f_twx = l.f_twx;
+  sb.f_Fx = l.f_Fx;
+  sb.f_Bx = l.f_Bx;
+  sb.f_lx = l.f_lx;
+  sb.f_twy = l.f_twy;
+  sb.f_Fy = l.f_Fy;
+  sb.f_By = l.f_By;
+  sb.f_ly = l.f_ly;
+  sb.fdat = reinterpret_cast<const float*>(base + l.off_F);
+  sb.fx = reinterpret_cast<float2*>(base + l.off_X);
   if (sb.kron) {
     double lam[3] = {0.0, 0.0, 0.0};
     if (d->equation == STDG_ADVECTION) {
@@ -773,6 +908,13 @@ stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* d, const doubl
     }
     std::vector<float> kd = kron_data(d, l.n, l.s, l.nd, lam);
     BCK(b, cudaMemcpy(base + l.off_K, kd.data(), kd.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (l.fdm) {
+      std::vector<float> fd;
+      if (!fdm_data(d, l, lam, &fd)) return bfail(b, STDG_ERR_NOT_CONVERGED, "fdm: eigensolve did not converge");
+      BCK(b, cudaMemcpy(base + l.off_F, fd.data(), fd.size() * sizeof(float), cudaMemcpyHostToDevice));
+      sb.kron = 0;
+      sb.fdm = 1;
+    }
   }
   hs.epb64 = pick_epb(l.dim, d->equation, 8, kModeResidual, l.n, l.s, l.nelem, l.nd);
   hs.epb32 = pick_epb(l.dim, d->equation, 4, kModeJvExact, l.n, l.s, l.nelem, l.nd);
@@ -798,7 +940,9 @@ stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* d, const doubl
   std::memset(&c, 0, sizeof(c));
   c.phase = kPhResid;
   c.m = l.m;
-  c.newton_maxit = d->newton_maxit;
+  // each cycle of at most m FGMRES iterations ends with a re-linearisation; the cap on cycles gives
+  // a slot the GMRES-iteration budget of the single-slab solver, newton_maxit x gmres_maxit
+  c.newton_maxit = d->newton_maxit * std::max(1, (d->gmres_maxit + l.m - 1) / l.m);
   c.rtol = d->newton_rtol;
   c.atol = d->newton_atol;
   c.gmres_rtol = d->gmres_rtol;

@@ -59,6 +59,13 @@ struct SlotBuf {
   // kdat = [Vx^-1 | Vx | Vy^-1 | Vy] (n x n each) then P_k^-1 (s x s) per mode k of the element
   int kron, dim, n;
   const float* kdat;
+  // global fast-diagonalisation preconditioner (scalar slots on periodic grids whose element
+  // counts are powers of two; fdm = 1 replaces kron), see engine_fdm.cu:
+  // fdat = tw_x | F_x | B_x | lam_x | tw_y | F_y | B_y | lam_y (offsets below, in floats)
+  int fdm, fkx, fky, fny, flogx, flogy;
+  int f_twx, f_Fx, f_Bx, f_lx, f_twy, f_Fy, f_By, f_ly;
+  const float* fdat;
+  float2* fx;  // complex scratch of L values, [kx][jx][m][ey][iy]
 };
 
 // Scalar solver state of one slot (FP64).
@@ -95,7 +102,20 @@ struct EngLaunch {
   double* partials;  // kEngRows per chunk item
   int* tick;         // tick counter (device), advanced by the last launch of a tick
   int any_kron;      // some slot uses the element tensor-product preconditioner
+  // global fast-diagonalisation preconditioner: work items (slot, ey s + m) of the x passes and
+  // (slot, kx n + jx) of the y/temporal pass, and the shared memory of each pass
+  const EngItem* fdm_rows;
+  const int* n_fdm_rows;
+  const EngItem* fdm_cols;
+  const int* n_fdm_cols;
+  int any_fdm, fdm_grid_rows, fdm_grid_cols;
+  size_t fdm_smem_a, fdm_smem_b, fdm_smem_c;
 };
+
+// Launches of the global preconditioner for the slots in kUpdInit / kUpdGSZ (engine_fdm.cu).
+cudaError_t eng_fdm_apply(const EngLaunch& L, cudaStream_t st);
+// Shared-memory attributes of its kernels (outside stream capture).
+cudaError_t eng_fdm_prepare(const EngLaunch& L);
 
 // Whether slot b takes part in the current tick (size-aware sharing: a slot much larger
 // than the sharing quantum advances only every stride-th tick).

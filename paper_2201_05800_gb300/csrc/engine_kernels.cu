@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kEngThreads) eng_update_kernel(const __grid_co
       } else if (mode == kUpdExtract) {
         b.uprev[e * tnode + q] = b.U[base + (size_t)(s - 1) * tnode];
       }
-      if (apply_z && !b.kron) {  // Kron slots: z is formed by eng_kron_kernel
+      if (apply_z && !b.kron && !b.fdm) {  // Kron / fdm slots: z is formed by their own kernels
         const float* P = b.Pinv + (e * s * s) * nd + node;
         for (int m = 0; m < s; ++m) {
           float z = 0.f;
@@ -498,6 +498,10 @@ cudaError_t eng_tick_tail(const EngLaunch& L, cudaStream_t st) {
   eng_control_kernel<<<(L.n_active + warps_per_block - 1) / warps_per_block, kEngThreads, 0, st>>>(L);
   eng_update_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
   if (L.any_kron) eng_kron_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
+  if (L.any_fdm) {
+    const cudaError_t e = eng_fdm_apply(L, st);
+    if (e != cudaSuccess) return e;
+  }
   eng_tick_kernel<<<1, 1, 0, st>>>(L.tick);
   return cudaGetLastError();
 }

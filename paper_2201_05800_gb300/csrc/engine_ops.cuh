@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(128) eng_build_kernel(const __grid_constant__ 
     const EngItem item = L.chunk_items[it];
     if (L.ctl[item.slot].phase != kPhResid) continue;
     const SlotBuf& b = L.buf[item.slot];
-    if (!eng_runs(L, b) || b.kron) continue;
+    if (!eng_runs(L, b) || b.kron || b.fdm) continue;
     const long long e0 = (long long)item.idx * b.chunk_elems;
     const long long e1 = e0 + b.chunk_elems < b.nelem ? e0 + b.chunk_elems : b.nelem;
     for (long long idx = e0 * b.nd + threadIdx.x; idx < e1 * b.nd; idx += blockDim.x)

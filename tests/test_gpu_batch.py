@@ -208,3 +208,56 @@ def test_element_preconditioner_cuts_iterations_on_stiff_viscous_slots(S):
                     assert rel_lgl(p, p.from_ext(B.get_slab(sl)), _oracle(p, u0)) <= 1e-8
     for a, b in zip(its[S.PRECOND_TEMPORAL_MASS], its[S.PRECOND_POINT_BLOCK]):
         assert a < 0.6 * b, its
+
+
+def test_global_preconditioner_is_exact_for_pure_diffusion(S):
+    """u_t = nu (u_xx + u_yy) (advection with zero velocity, viscous): the global fast-
+    diagonalisation preconditioner of scalar slots inverts the slab Jacobian exactly (the linear
+    operator has no convective part), so every Newton step needs one or two FGMRES iterations
+    (FP32 rounding of the transforms); the slab reaches the oracle's."""
+    prob = Problem(dim=2, cells=(8, 16), N=4, s=4, eq="advection", dt=0.02, adv=(0.0, 0.0), nu=0.05)
+    X = prob.grid.coordinates()
+    u0 = (np.sin(2 * np.pi * X[0]) * np.cos(4 * np.pi * X[1]) + 0.3 * np.sin(6 * np.pi * X[1]))[..., None]
+    with S.Batch(2, S.ADVECTION, 2, 256 << 20) as B:
+        sl = B.add(prob.config(**WORK), np.ascontiguousarray(u0).ravel())
+        assert B.run(20000) == 0
+        done, status, st = B.query(sl)
+        assert status == 0 and st["newton_its"] >= 1, st
+        assert st["gmres_its"] <= 2 * st["newton_its"], st
+        assert rel_lgl(prob, prob.from_ext(B.get_slab(sl)), _oracle(prob, u0)) <= 1e-8
+
+
+def test_global_preconditioner_on_a_1d_viscous_advection_slot(S):
+    """1D advection-diffusion (16 elements, N = 5, s = 5): the global preconditioner handles the
+    dissipation of the upwind flux as well; few iterations, the oracle's slab."""
+    prob = Problem(dim=1, cells=(16,), N=5, s=5, eq="advection", dt=0.05, adv=(1.0,), nu=0.02)
+    u0 = inputs.sine(prob.grid.coordinates()[0])
+    with S.Batch(1, S.ADVECTION, 2, 64 << 20) as B:
+        sl = B.add(prob.config(**WORK), np.ascontiguousarray(u0).ravel())
+        assert B.run(20000) == 0
+        done, status, st = B.query(sl)
+        assert status == 0, st
+        assert st["gmres_its"] <= 12 * st["newton_its"], st
+        assert rel_lgl(prob, prob.from_ext(B.get_slab(sl)), _oracle(prob, u0)) <= 1e-8
+
+
+def test_stiffest_workload_instances_converge(S):
+    """The stiffest instances of the batched viscous Burgers workload (N = 6, s = 4 or 5,
+    nu ~ 0.03-0.09 on 32^2 and 64^2 grids, dt/2 times the largest element eigenvalue above 1e4),
+    which the element-local preconditioner left at the Newton cap: with the global preconditioner
+    each converges, alone and together, with the same result."""
+    import bench
+    items = bench._burgers_instances(S, 301)
+    ids = (113, 186, 264, 280, 300)
+    with S.Batch(2, S.BURGERS, 8, 8 << 30) as B:
+        slots = [B.add(items[i][0], items[i][1]) for i in ids]
+        assert B.run(200000) == 0
+        mixed = []
+        for i, sl in zip(ids, slots):
+            done, status, st = B.query(sl)
+            assert done and status == 0, (i, st)
+            mixed.append(B.get_state(sl))
+    with S.Batch(2, S.BURGERS, 2, 4 << 30) as B:
+        sl = B.add(items[ids[0]][0], items[ids[0]][1])
+        assert B.run(200000) == 0
+        assert np.array_equal(B.get_state(sl), mixed[0])
