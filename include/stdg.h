@@ -74,7 +74,10 @@ typedef enum {
 
 enum { STDG_ADVECTION = 0, STDG_EULER = 1, STDG_BURGERS = 2 };
 enum { STDG_FLUX_RUSANOV = 0 };             /* Eq. flux:llf; upwind for advection       */
-enum { STDG_FP64 = 0, STDG_MIXED_FP32 = 1 };/* precision of Jv and the GMRES basis       */
+/* precision of Jv and the GMRES basis; STDG_MIXED_BF16: as STDG_MIXED_FP32 with the volume
+ * contractions of the exact Jv on the tensor cores (BF16 inputs, FP32 accumulation), built for
+ * the 3D Euler N = 3, s = 3 shape with STDG_JV_EXACT (other configurations: invalid) */
+enum { STDG_FP64 = 0, STDG_MIXED_FP32 = 1, STDG_MIXED_BF16 = 2 };
 enum { STDG_JV_FD = 0, STDG_JV_EXACT = 1 }; /* finite-difference JFNK or forward mode    */
 enum { STDG_HOST = 0, STDG_DEVICE = 1 };
 /* GMRES preconditioning of J dU = -R.  STDG_PRECOND_TEMPORAL_MASS solves the
@@ -115,7 +118,7 @@ typedef struct {
   double gamma;             /* ratio of specific heats (Euler)                           */
   int flux;                 /* STDG_FLUX_RUSANOV                                         */
   double dt;                /* slab length Delta t_n > 0                                 */
-  int precision;            /* STDG_FP64 | STDG_MIXED_FP32                               */
+  int precision;            /* STDG_FP64 | STDG_MIXED_FP32 | STDG_MIXED_BF16             */
   int jv_mode;              /* STDG_JV_FD | STDG_JV_EXACT                                */
   double newton_rtol;       /* stop when ||R||_2 <= max(rtol ||R(U0)||_2, atol)          */
   double newton_atol;

@@ -187,7 +187,11 @@ stdg_status validate(const stdg_config_desc* d, std::string* why) {
   if (d->flux != STDG_FLUX_RUSANOV) return bad("unknown flux");
   if (!(d->dt > 0) || !std::isfinite(d->dt)) return bad("dt must be positive");
   if (d->equation == STDG_EULER && !(d->gamma > 1.0)) return bad("gamma must exceed 1");
-  if (d->precision != STDG_FP64 && d->precision != STDG_MIXED_FP32) return bad("unknown precision");
+  if (d->precision != STDG_FP64 && d->precision != STDG_MIXED_FP32 && d->precision != STDG_MIXED_BF16)
+    return bad("unknown precision");
+  if (d->precision == STDG_MIXED_BF16 &&
+      !(d->dim == 3 && d->equation == STDG_EULER && d->N == 3 && d->s == 3 && d->jv_mode == STDG_JV_EXACT))
+    return bad("STDG_MIXED_BF16 is built for the 3D Euler N = 3, s = 3 shape with STDG_JV_EXACT");
   if (d->jv_mode != STDG_JV_FD && d->jv_mode != STDG_JV_EXACT) return bad("unknown jv_mode");
   if (d->newton_maxit < 1 || d->gmres_maxit < 1) return bad("maxit must be >= 1");
   if (d->gmres_m < 1 || d->gmres_m > kMaxGmresM) return bad("gmres_m must be 1..31");
@@ -337,7 +341,7 @@ stdg_status op_jv_t(stdg_ctx* c, const KView<T>& kv, const T* U, const T* F0, co
   if constexpr (std::is_same<T, float>::value) {
     if (mode == kModeJvExact) {
       bool handled = false;
-      CK(c, launch_jv_tangent(c->dim, c->d.equation, k, c->st, &handled));
+      CK(c, launch_jv_tangent(c->dim, c->d.equation, k, c->st, &handled, c->d.precision == STDG_MIXED_BF16));
       if (handled) return STDG_OK;
     }
   }
@@ -613,7 +617,7 @@ stdg_status stdg_create(const stdg_config_desc* desc, void* cuda_stream, stdg_ct
   if (!desc) return STDG_ERR_INVALID_ARG;
   std::string why;
   if (validate(desc, &why) != STDG_OK) return STDG_ERR_INVALID_ARG;
-  const bool mixed = desc->precision == STDG_MIXED_FP32;
+  const bool mixed = desc->precision != STDG_FP64;
   stdg_ctx* c = new stdg_ctx();
   c->d = *desc;
   c->st = static_cast<cudaStream_t>(cuda_stream);
@@ -832,7 +836,7 @@ stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
   const bool extrap = c->d.predictor == STDG_PREDICTOR_EXTRAPOLATE && c->have_slab;
   if (extrap) PK(c, 3, temporal_mix(c->X1, c->U, c->ext, c->nelem, c->s, blk, c->st));
   PK(c, 3, broadcast_slab<double>(c->U, c->uprev, c->nelem, c->s, blk, c->st));
-  const bool mixed0 = c->d.precision == STDG_MIXED_FP32;
+  const bool mixed0 = c->d.precision != STDG_FP64;
   // the residual kernel also writes the first Krylov vector into the basis of the working
   // precision and returns |R|, |U| (FD step) and that vector's norm
   double* v0d = mixed0 ? nullptr : c->V;
@@ -859,7 +863,7 @@ stdg_status stdg_advance_slab(stdg_ctx* c, stdg_slab_stats* stats) {
       ++S.residual_evals;
     }
   }
-  const bool mixed = c->d.precision == STDG_MIXED_FP32;
+  const bool mixed = c->d.precision != STDG_FP64;
   stdg_status status = STDG_OK;
   while (true) {
     if (!std::isfinite(res)) {

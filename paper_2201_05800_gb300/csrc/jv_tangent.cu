@@ -1,6 +1,7 @@
 // Instantiations and launcher of the tangent-only FP32 Jacobian-vector kernel
 // (jv_tangent.cuh) for the Euler shapes of the 2D vortex (n = 5, s = 4) and the
-// 3D density wave (n = 4, s = 3).
+// 3D density wave (n = 4, s = 3), the latter also with the volume contractions
+// on the tensor cores (BF16 inputs, FP32 accumulation).
 #include "jv_tangent.cuh"
 #include "ops.h"
 
@@ -8,11 +9,11 @@ namespace stdg {
 
 namespace {
 
-template <int DIM, int NP, int NS, int E>
+template <int DIM, int NP, int NS, int E, bool TC = false>
 cudaError_t launch_one(const OpArgs<float>& k, cudaStream_t st) {
   constexpr int ND = ipow_c(NP, DIM);
-  constexpr size_t smem = jv_tangent_smem_bytes<DIM, NP, NS, E>();
-  auto kern = jv_tangent_kernel<DIM, NP, NS, E>;
+  constexpr size_t smem = jv_tangent_smem_bytes<DIM, NP, NS, E, TC>();
+  auto kern = jv_tangent_kernel<DIM, NP, NS, E, TC>;
   static_assert(smem <= 227 * 1024, "tile exceeds shared memory");
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -31,7 +32,8 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 // J(U) v in FP32 by the tangent-only kernel when the shape has an instantiation and the
 // slabs satisfy the bulk-copy alignment (16-byte base addresses; element tiles are whole
 // multiples of 16 bytes for these shapes).  *handled = false: nothing was launched.
-cudaError_t launch_jv_tangent(int dim, int eq, const OpArgs<float>& k, cudaStream_t st, bool* handled) {
+cudaError_t launch_jv_tangent(int dim, int eq, const OpArgs<float>& k, cudaStream_t st, bool* handled,
+                              bool tensor_cores) {
   *handled = false;
   if (eq != STDG_EULER || !k.U || !k.v || !k.out || k.nelem < 1) return cudaSuccess;
   if (!aligned16(k.U) || !aligned16(k.v)) return cudaSuccess;
@@ -41,7 +43,7 @@ cudaError_t launch_jv_tangent(int dim, int eq, const OpArgs<float>& k, cudaStrea
   }
   if (dim == 3 && k.n == 4 && k.s == 3) {
     *handled = true;
-    return launch_one<3, 4, 3, 1>(k, st);
+    return tensor_cores ? launch_one<3, 4, 3, 2, true>(k, st) : launch_one<3, 4, 3, 1>(k, st);
   }
   return cudaSuccess;
 }

@@ -27,6 +27,7 @@
 // two elements (the neighbour's side from global memory).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "common.cuh"
@@ -74,16 +75,81 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long l
   return false;
 }
 
-// Shared-memory bytes of one CTA of jv_tangent_kernel.
-template <int DIM, int NP, int NS, int E>
+// Line pitch of the flux-tangent store: a line of NP values padded to whole 16-byte words.
+__host__ __device__ constexpr int jv_line_pitch(int np) { return (np + 3) / 4 * 4; }
+
+// ---------------------------------------------------------------- tensor cores (tcgen05)
+// One CTA-wide BF16 x BF16 -> FP32 MMA of M = 128, N = 16, K = 16 with the operands in shared
+// memory (K-major, no swizzle: 8-row x 16-byte core matrices, K chunks kTcLbo bytes apart,
+// 8-row groups kTcSbo bytes apart) and the accumulator in tensor memory (row i = TMEM lane i,
+// column j = TMEM column j).
+constexpr unsigned kTcLbo = 128, kTcSbo = 256;
+constexpr unsigned kTcCols = 64;  // TMEM columns allocated per CTA (three 16-column accumulators)
+
+__device__ __forceinline__ unsigned tc_offset(int row, int k) {  // byte offset of (row, k), bf16
+  return (unsigned)((row >> 3) * kTcSbo + (k >> 3) * kTcLbo + (row & 7) * 16 + (k & 7) * 2);
+}
+__device__ __forceinline__ uint64_t tc_desc(const void* smem) {
+  const uint64_t a = smem_u32(smem);
+  return ((a >> 4) & 0x3FFFull) | ((uint64_t)(kTcLbo >> 4) << 16) | ((uint64_t)(kTcSbo >> 4) << 32) |
+         (1ull << 46);  // descriptor version 1, no swizzle, base offset 0
+}
+// instruction descriptor: D FP32, A and B BF16, both K-major, N = 16, M = 128
+constexpr unsigned kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tmem_alloc(unsigned* dst) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(kTcCols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(unsigned taddr) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcCols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_mma(unsigned d_tmem, uint64_t adesc, uint64_t bdesc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(0)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes 32 (w % 4) ..)
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory bytes of one CTA of jv_tangent_kernel (TC: plus the tensor-core operands, BF16
+// A (128 x 16) and B (16 x 16) per direction at a 128-byte boundary, and the volume terms read
+// back from tensor memory, one slot per direction).
+template <int DIM, int NP, int NS, int E, bool TC = false>
 __host__ __device__ constexpr size_t jv_tangent_smem_bytes() {
   constexpr int R = DIM + 2;
   constexpr int ND = ipow_c(NP, DIM);
-  return sizeof(float) * ((size_t)2 * E * NS * ND * R       // staged U and v tiles
-                          + (size_t)E * NS * DIM * R * ND   // flux tangents
-                          + (size_t)2 * E * NS * DIM * ND   // wave speeds and tangents
-                          + (size_t)E * NS * DIM * R * ND   // face corrections per direction
-                          + (size_t)DIM * NP * NP);         // (2/h_a) D
+  constexpr int LINES = (ND / NP) * jv_line_pitch(NP);
+  constexpr size_t base = sizeof(float) * ((size_t)2 * E * NS * ND * R          // staged U and v tiles
+                                           + (size_t)E * NS * DIM * R * LINES   // flux tangents, per direction
+                                           + (size_t)2 * E * NS * DIM * ND      // wave speeds and tangents
+                                           + (size_t)E * NS * DIM * R * ND      // face corrections per direction
+                                           + (size_t)DIM * NP * jv_line_pitch(NP));  // (2/h_a) D, rows padded
+  return TC ? (base + 127) / 128 * 128 + (size_t)DIM * (128 * 16 + 16 * 16) * 2 +
+                  sizeof(float) * (size_t)DIM * E * NS * R * ND
+            : base;
 }
 
 // x[a] for a runtime index a without local memory (unrolled selects).
@@ -101,7 +167,7 @@ struct EulerTangent {
   static constexpr int R = DIM + 2;
   float ir, dir, v[DIM], dv[DIM], p, dp;
   __device__ __forceinline__ void init(const float (&u)[R], const float (&du)[R], float gamma) {
-    ir = 1.0f / u[0];
+    ir = __fdividef(1.0f, u[0]);  // hardware reciprocal: ~2 ulp, below the FP32 rounding of J v
     dir = -du[0] * ir * ir;
     float ke = 0.f, dke = 0.f;  // |m|^2 / rho and its tangent
 #pragma unroll
@@ -135,37 +201,60 @@ struct EulerTangent {
   }
   __device__ __forceinline__ void sound(float gamma, float* c, float* dc) const {
     const float q = gamma * (p * ir);
-    *c = sqrtf(q);
+    const float rq = rsqrtf(q);  // hardware 1/sqrt: c = q / sqrt(q), dc = dq / (2 sqrt(q))
+    *c = q * rq;
     const float dq = gamma * fmaf(dp, ir, p * dir);
-    *dc = dq * (0.5f / *c);
+    *dc = dq * (0.5f * rq);
   }
 };
 
 // out = J(U) v for elements [blockIdx.x * E, ...) of the slab.  FP32; k.U, k.v, k.out are
 // FP32 slabs [e][m][node][c]; blockDim.x >= E * NS * ND.
-template <int DIM, int NP, int NS, int E>
+// TC: the volume contractions on the tensor cores (tcgen05, BF16 inputs, FP32 accumulation):
+// per direction a one M = 128 x N = 16 x K = 16 MMA whose rows are (element, component,
+// temporal node, group of four lines along e_a) and whose K index is (line in the group, node on
+// the line); B = I_4 (x) (-(2/h_a) D)^T.  3D, n = 4 only (E R NS 4 <= 128 rows).
+template <int DIM, int NP, int NS, int E, bool TC = false>
 __global__ void __launch_bounds__((E * NS * ipow_c(NP, DIM) + 31) / 32 * 32)
     jv_tangent_kernel(const __grid_constant__ OpArgs<float> k) {
   constexpr int R = DIM + 2;
   constexpr int ND = ipow_c(NP, DIM);
   constexpr int NF = ND / NP;
   constexpr int TILE = NS * ND * R;
+  constexpr int LP = jv_line_pitch(NP);  // pitch of one line of the flux-tangent store
+  constexpr int LINES = NF * LP;         // one component of one direction: NF lines
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* su = reinterpret_cast<float*>(smem_raw);  // [E][NS][ND][R]
   float* sv = su + E * TILE;                       // [E][NS][ND][R]
-  float* sf = sv + E * TILE;                       // [E][NS][DIM][R][ND]
-  float* sl = sf + E * NS * DIM * R * ND;          // [E][NS][DIM][ND]
+  // flux tangents of direction a, line-major: the NP values along e_a of line q at
+  // [((el NS + m) DIM + a) R + c][q LP + i_a]; the line of a face point fidx is q = fidx
+  float* sf = sv + E * TILE;
+  float* sl = sf + E * NS * DIM * R * LINES;       // [E][NS][DIM][ND]
   float* sdl = sl + E * NS * DIM * ND;             // [E][NS][DIM][ND]
   float* sc = sdl + E * NS * DIM * ND;             // [E][NS][DIM][R][ND]
-  float* sD = sc + E * NS * DIM * R * ND;          // [DIM][NP][NP]
+  float* sD = sc + E * NS * DIM * R * ND;          // [DIM][NP][LP]
+  static_assert(TILE % 4 == 0, "element tiles must be whole 16-byte words (bulk copy)");
+  static_assert(!TC || (DIM == 3 && NP == 4 && E * R * NS * 4 <= 128 && E * NS * ND >= 128),
+                "tensor-core volume: 3D, n = 4, at most 128 MMA rows and four full warps");
+  constexpr size_t kBase = jv_tangent_smem_bytes<DIM, NP, NS, E, false>();
+  unsigned char* tcA = smem_raw + (kBase + 127) / 128 * 128;  // [a][128 x 16] bf16, core-matrix layout
+  unsigned char* tcB = tcA + DIM * 128 * 16 * 2;               // [a][16 x 16] bf16
+  float* svol = reinterpret_cast<float*>(tcB + DIM * 16 * 16 * 2);  // [a][E][NS][R][ND]
+  __shared__ __align__(8) uint64_t bar_mma;
+  __shared__ unsigned tmem_base;
+  __shared__ int mma_ok;
+  static_assert((2 * E * TILE + E * NS * DIM * R * LINES + 2 * E * NS * DIM * ND + E * NS * DIM * R * ND) % 4 == 0,
+                "the D rows are read as 16-byte words");
   __shared__ __align__(8) uint64_t bar;
   __shared__ int staged;
+  __shared__ long long snb[E * DIM * 2];  // periodic neighbour element of (el, a, side)
 
   const int tid = threadIdx.x;
   const long long e0 = (long long)blockIdx.x * E;
   const int nel = (int)((k.nelem - e0) < E ? (k.nelem - e0) : E);
   if (tid == 0) {
     mbar_init(&bar, 1);
+    if (TC) mbar_init(&bar_mma, 1);
   }
   __syncthreads();
   if (tid == 0) {
@@ -174,9 +263,21 @@ __global__ void __launch_bounds__((E * NS * ipow_c(NP, DIM) + 31) / 32 * 32)
     bulk_g2s(su, k.U + e0 * TILE, bytes, &bar);
     bulk_g2s(sv, k.v + e0 * TILE, bytes, &bar);
   }
-  for (int i = tid; i < DIM * NP * NP; i += blockDim.x) {
-    const int a = i / (NP * NP), q = i % (NP * NP);
-    sD[i] = k.ginv[a] * k.D[q / NP][q % NP];
+  for (int i = tid; i < DIM * NP * LP; i += blockDim.x) {
+    const int a = i / (NP * LP), r = (i / LP) % NP, j = i % LP;
+    sD[i] = j < NP ? k.ginv[a] * k.D[r][j] : 0.f;
+  }
+  // neighbour table of the tile (element index e = (ez K1 + ey) K0 + ex, periodic)
+  if (tid < nel * DIM * 2) {
+    const int side = tid & 1, a = (tid >> 1) % DIM, fel = (tid >> 1) / DIM;
+    const long long e = e0 + fel;
+    const long long K0 = k.K[0], K1 = k.K[1], K2 = k.K[2];
+    long long ex = e % K0, ey = (e / K0) % K1, ez = e / (K0 * K1);
+    const long long step = side ? 1 : -1;
+    if (a == 0) ex = (ex + step + K0) % K0;
+    else if (a == 1) ey = (ey + step + K1) % K1;
+    else ez = (ez + step + K2) % K2;
+    snb[tid] = (ez * K1 + ey) * K0 + ex;
   }
   if (tid == 0) {
     bool ok = mbar_wait(&bar, 0, kWaitLimit);
@@ -189,6 +290,24 @@ __global__ void __launch_bounds__((E * NS * ipow_c(NP, DIM) + 31) / 32 * 32)
   __syncthreads();
   if (!staged) return;
   mbar_wait(&bar, 0, kWaitLimit);  // completed: acquire the staged data in every thread
+  if constexpr (TC) {
+    if (tid < 32) {  // one warp allocates (and later frees) the accumulators
+      tmem_alloc(&tmem_base);
+      tc_fence_before();
+    }
+    // B_a = I_4 (x) (-(2/h_a) D)^T: B[n = 4 l' + i][kk = 4 l + j] = [l = l'] (-(2/h_a) D[i][j])
+    for (int t = tid; t < DIM * 256; t += blockDim.x) {
+      const int a = t >> 8, n = (t >> 4) & 15, kk = t & 15;
+      const float b = (n >> 2) == (kk >> 2) ? -k.ginv[a] * k.D[n & 3][kk & 3] : 0.f;
+      *reinterpret_cast<__nv_bfloat16*>(tcB + a * 512 + tc_offset(n, kk)) = __float2bfloat16_rn(b);
+    }
+    // rows past the CTA's elements are zero
+    for (int t = tid; t < DIM * 128 * 16; t += blockDim.x) {
+      const int a = t / 2048, row = (t / 16) % 128, kk = t % 16;
+      if (row >= nel * R * NS * 4)
+        *reinterpret_cast<__nv_bfloat16*>(tcA + a * 4096 + tc_offset(row, kk)) = __float2bfloat16_rn(0.f);
+    }
+  }
 
   const int item = tid;
   const bool active = item < nel * NS * ND;
@@ -197,7 +316,6 @@ __global__ void __launch_bounds__((E * NS * ipow_c(NP, DIM) + 31) / 32 * 32)
   const int node = item % ND;
   const int q1 = node / NP, q2 = q1 / NP;
   const int idx[3] = {node % NP, DIM > 1 ? q1 % NP : 0, DIM > 2 ? q2 : 0};
-  const int strides[3] = {1, NP, NP * NP};
   const float gamma = k.gamma;
 
   // ---- 0. primitives, flux tangents and wave speeds at (el, m, node)
@@ -218,32 +336,67 @@ __global__ void __launch_bounds__((E * NS * ipow_c(NP, DIM) + 31) / 32 * 32)
     for (int a = 0; a < DIM; ++a) {
       float df[R];
       P.flux_tangent(u, du, a, df);
-      float* sfa = sf + (((el * NS + m) * DIM + a) * R) * ND + node;
+      // line q of node along e_a and position i_a on it
+      const int ia = idx[a];
+      const int q = a == 0 ? idx[1] + NP * idx[2] : (a == 1 ? idx[0] + NP * idx[2] : idx[0] + NP * idx[1]);
+      float* sfa = sf + (((el * NS + m) * DIM + a) * R) * LINES + q * LP + ia;
 #pragma unroll
-      for (int c = 0; c < R; ++c) sfa[c * ND] = df[c];
+      for (int c = 0; c < R; ++c) sfa[c * LINES] = df[c];
+      if constexpr (TC) {  // the MMA operand: row (el, c, m, q / 4), column 4 (q % 4) + i_a
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+          const int row = ((el * R + c) * NS + m) * 4 + (q >> 2);
+          *reinterpret_cast<__nv_bfloat16*>(tcA + a * 4096 + tc_offset(row, 4 * (q & 3) + ia)) =
+              __float2bfloat16_rn(df[c]);
+        }
+      }
       float lam, dlam;
       P.speed(a, gamma, c0, dc0, &lam, &dlam);
       sl[((el * NS + m) * DIM + a) * ND + node] = lam;
       sdl[((el * NS + m) * DIM + a) * ND + node] = dlam;
     }
   }
+  if constexpr (TC) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands -> tensor cores
   __syncthreads();
 
-  // ---- 1a. volume term (tangent), kept in registers for the output phase
+  // ---- 1a. volume term (tangent), kept in registers for the output phase (TC: three MMAs,
+  //          issued here and read back after the face points)
   float acc[R];
 #pragma unroll
   for (int c = 0; c < R; ++c) acc[c] = 0.f;
-  if (active) {
+  if constexpr (TC) {
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) tc_mma(tmem_base + 16 * a, tc_desc(tcA + a * 4096), tc_desc(tcB + a * 512));
+      tc_commit(&bar_mma);
+    }
+  }
+  if (!TC && active) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const int ia = idx[a];
-      const int base = node - ia * strides[a];
-      const float* Da = sD + (a * NP + ia) * NP;
-      const float* sfa = sf + (((el * NS + m) * DIM + a) * R) * ND + base;
+      const int q = a == 0 ? idx[1] + NP * idx[2] : (a == 1 ? idx[0] + NP * idx[2] : idx[0] + NP * idx[1]);
+      float Da[LP];
+      const float4* Dv = reinterpret_cast<const float4*>(sD + (a * NP + ia) * LP);
 #pragma unroll
-      for (int c = 0; c < R; ++c)
+      for (int w = 0; w < LP / 4; ++w) {
+        const float4 d4 = Dv[w];
+        Da[4 * w] = d4.x, Da[4 * w + 1] = d4.y, Da[4 * w + 2] = d4.z, Da[4 * w + 3] = d4.w;
+      }
+      const float* sfa = sf + (((el * NS + m) * DIM + a) * R) * LINES + q * LP;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) acc[c] = fmaf(-Da[j], sfa[c * ND + j * strides[a]], acc[c]);
+      for (int c = 0; c < R; ++c) {
+        const float4* fv = reinterpret_cast<const float4*>(sfa + c * LINES);
+#pragma unroll
+        for (int w = 0; w < LP / 4; ++w) {
+          const float4 f4 = fv[w];
+          const float f[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj)
+            if (4 * w + jj < NP) acc[c] = fmaf(-Da[4 * w + jj], f[jj], acc[c]);
+        }
+      }
     }
   }
   // ---- 1b. face points: items (el, m, a, side, fidx), correction of the own node
@@ -260,19 +413,11 @@ __global__ void __launch_bounds__((E * NS * ipow_c(NP, DIM) + 31) / 32 * 32)
     const int ia_own = side ? NP - 1 : 0;
     const int own = lo + ia_own * sa + hi * sa * NP;
     const int nbr = lo + (NP - 1 - ia_own) * sa + hi * sa * NP;
-    // periodic neighbour element across the face (element index e = (ez K1 + ey) K0 + ex)
-    const int e = (int)(e0 + fel);
-    const int K0 = k.K[0], K1 = k.K[1], K2 = k.K[2];
-    int ex = e % K0, ey = (e / K0) % K1, ez = e / (K0 * K1);
-    const int step = side ? 1 : -1;
-    if (a == 0) ex = (ex + step + K0) % K0;
-    else if (a == 1) ey = (ey + step + K1) % K1;
-    else ez = (ez + step + K2) % K2;
-    const long long en = ((long long)ez * K1 + ey) * K0 + ex;
+    const long long en = snb[(fel * DIM + a) * 2 + side];
     // own side (staged)
     const float* uo = su + ((fel * NS + fm) * ND + own) * R;
     const float* duo = sv + ((fel * NS + fm) * ND + own) * R;
-    const float* sfo = sf + (((fel * NS + fm) * DIM + a) * R) * ND + own;
+    const float* sfo = sf + (((fel * NS + fm) * DIM + a) * R) * LINES + fidx * LP + ia_own;
     const float lo_l = sl[((fel * NS + fm) * DIM + a) * ND + own];
     const float lo_d = sdl[((fel * NS + fm) * DIM + a) * ND + own];
     // neighbour side (global memory)
@@ -306,12 +451,46 @@ __global__ void __launch_bounds__((E * NS * ipow_c(NP, DIM) + 31) / 32 * 32)
     for (int c = 0; c < R; ++c) {
       // side 1: -(g/2)(d(df) - dlam du - lam d(du)), du = u_nbr - u_own, df = f_nbr - f_own
       // side 0: +(g/2)(d(df) - dlam du - lam d(du)), du = u_own - u_nbr, df = f_nbr - f_own
-      const float ddf = dfn[c] - sfo[c * ND];
+      const float ddf = dfn[c] - sfo[c * LINES];
       const float jv = side ? un[c] - uo[c] : uo[c] - un[c];
       const float djv = side ? dun[c] - duo[c] : duo[c] - dun[c];
       const float t = ddf - fmaf(dlam, jv, lam * djv);
       sco[c * ND] = side ? -g * t : g * t;
     }
+  }
+  if constexpr (TC) {
+    // accumulators complete (bounded wait), then warps 0-3 read lanes 0-127 back to shared memory
+    if (tid == 0) {
+      bool ok = mbar_wait(&bar_mma, 0, kWaitLimit);
+      if (!ok) {
+        if (k.err) atomicOr(k.err, 1u);
+        mbar_wait(&bar_mma, 0, kWaitLimit);
+      }
+      mma_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (tid < 128 && mma_ok) {
+      const int row = tid;
+      const int g = row & 3, rm = (row >> 2) % NS, rc = (row / (4 * NS)) % R, rel = row / (4 * NS * R);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        float v[16];
+        tmem_ld16(tmem_base + ((unsigned)(tid & ~31) << 16) + 16 * a, v);
+        if (rel < nel) {
+#pragma unroll
+          for (int nn = 0; nn < 16; ++nn) {
+            const int q = 4 * g + (nn >> 2), i = nn & 3;
+            const int node = a == 0 ? i + 4 * q : (a == 1 ? (q & 3) + 4 * i + 16 * (q >> 2) : q + 16 * i);
+            svol[(((a * E + rel) * NS + rm) * R + rc) * ND + node] = v[nn];
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid < 32) tmem_dealloc(tmem_base);
+    if (!mma_ok) return;
   }
   __syncthreads();
 
@@ -326,6 +505,10 @@ __global__ void __launch_bounds__((E * NS * ipow_c(NP, DIM) + 31) / 32 * 32)
 #pragma unroll
     for (int c = 0; c < R; ++c) {
       float F = acc[c];
+      if constexpr (TC) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) F += svol[(((a * E + el) * NS + m) * R + c) * ND + node];
+      }
 #pragma unroll
       for (int a = 0; a < DIM; ++a)
         if (idx[a] == 0 || idx[a] == NP - 1) F += sc[(((el * NS + m) * DIM + a) * R + c) * ND + node];

@@ -17,7 +17,8 @@ template <class T> cudaError_t launch_euler2(int mode, const OpArgs<T>& k, cudaS
 template <class T> cudaError_t launch_euler3(int mode, const OpArgs<T>& k, cudaStream_t st);
 // Tangent-only FP32 exact J v for the specialised Euler shapes (jv_tangent.cu); *handled = false
 // when the shape or the alignment is not covered (nothing launched).
-cudaError_t launch_jv_tangent(int dim, int eq, const OpArgs<float>& k, cudaStream_t st, bool* handled);
+cudaError_t launch_jv_tangent(int dim, int eq, const OpArgs<float>& k, cudaStream_t st, bool* handled,
+                              bool tensor_cores = false);
 
 // Shared memory of one CTA (must match op_smem_bytes in operator.cuh).
 inline size_t operator_smem_bytes(int dim, int r, size_t tsize, int mode, int n, int s, int epb) {

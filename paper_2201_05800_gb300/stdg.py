@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_PKG, "libstdg.so")
 
 ADVECTION, EULER, BURGERS = 0, 1, 2
 FLUX_RUSANOV = 0
-FP64, MIXED_FP32 = 0, 1
+FP64, MIXED_FP32, MIXED_BF16 = 0, 1, 2
 JV_FD, JV_EXACT = 0, 1
 HOST, DEVICE = 0, 1
 PRECOND_NONE, PRECOND_TEMPORAL_MASS, PRECOND_POINT_BLOCK = 0, 1, 2

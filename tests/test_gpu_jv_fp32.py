@@ -80,3 +80,57 @@ def test_jv_fp32_full_size_density_wave_against_fp64_product(S):
         ref = ctx.jv(U32.double(), torch.from_numpy(u0).cuda(), v32.double())
         rel = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
         assert rel <= 2e-5, rel
+
+
+@pytest.mark.parametrize("cells", [(3, 2, 2), (4, 4, 4), (2, 1, 3)])
+def test_jv_bf16_tensor_cores_against_oracle(S, cells):
+    """STDG_MIXED_BF16 (3D Euler, n = 4, s = 3): the volume contractions run on the tensor cores
+    with BF16 inputs (relative rounding 2^-9 of each flux tangent and of each D entry) and FP32
+    accumulation.  Against the oracle: within 1e-2 relative (LGL-weighted L2), and above the FP32
+    kernel's error (the tensor-core path ran); ragged last tiles (odd element counts)."""
+    import torch
+    prob = Problem(dim=3, cells=cells, N=3, s=3, eq="euler", dt=0.02)
+    u_n = prob.rough_state(31, rel=0.05)
+    U = prob.rough_slab(u_n, 33)
+    v = inputs.random_array(U.shape, 37)
+    U32 = prob.ext(U).astype(np.float32)
+    v32 = prob.ext(v).astype(np.float32)
+    Uq = prob.from_ext(U32.astype(np.float64))
+    vq = prob.from_ext(v32.astype(np.float64))
+    ref = ost.jv_exact("stdg", prob.F, Uq, u_n, prob.dt, vq)
+    out = {}
+    for name, prec in (("bf16", S.MIXED_BF16), ("fp32", S.MIXED_FP32)):
+        with S.Context(prob.config(gmres_m=1, precision=prec, jv_mode=S.JV_EXACT)) as ctx:
+            o = ctx.jv_fp32(torch.from_numpy(U32).cuda(), torch.from_numpy(v32).cuda()).cpu().numpy()
+        out[name] = prob.from_ext(o.astype(np.float64))
+    nrm = ost.lgl_weighted_norm(prob.grid, ref)
+    e_bf16 = ost.lgl_weighted_norm(prob.grid, out["bf16"] - ref) / nrm
+    e_fp32 = ost.lgl_weighted_norm(prob.grid, out["fp32"] - ref) / nrm
+    assert e_bf16 <= 1e-2, e_bf16
+    assert e_fp32 <= 2e-5 and e_bf16 > 10 * e_fp32, (e_bf16, e_fp32)
+
+
+def test_bf16_mixed_slab_solve_reaches_the_oracle(S):
+    """3D density wave on 3^3 hexes, N = 3, s = 3: the BF16 tensor-core Jacobian-vector products
+    in the inner solve, FP64 Newton residuals refine: the slab is within 1e-8 of the oracle's at
+    the workload tolerances."""
+    prob = Problem(dim=3, cells=(3, 3, 3), N=3, s=3, eq="euler", dt=1.0)
+    X = prob.grid.coordinates()
+    u0 = inputs.density_wave(*X)
+    prob.dt = 0.5 * min(prob.grid.h) / 2.6
+    U_or = ost.solve_slab_newton_gmres("stdg", prob.F, u0, prob.dt, prob.s, rtol=1e-13, atol=1e-14,
+                                       gmres_tol=1e-11, gmres_m=40)
+    with S.Context(prob.config(precision=S.MIXED_BF16, jv_mode=S.JV_EXACT, newton_rtol=1e-10, gmres_rtol=0.05,
+                               newton_maxit=40)) as ctx:
+        ctx.set_state(np.ascontiguousarray(u0).ravel())
+        st = ctx.advance_slab()
+        U = prob.from_ext(ctx.get_slab())
+    assert st["status"] == 0, st
+    rel = ost.lgl_weighted_norm(prob.grid, U - U_or) / ost.lgl_weighted_norm(prob.grid, U_or)
+    assert rel <= 1e-8, (rel, st)
+
+
+def test_bf16_precision_is_refused_for_other_shapes(S):
+    prob = Problem(dim=2, cells=(4, 4), N=4, s=4, eq="euler", dt=0.02)
+    with pytest.raises(S.StdgError):
+        S.Context(prob.config(precision=S.MIXED_BF16, jv_mode=S.JV_EXACT))
