@@ -852,8 +852,7 @@ def _batched_leg(stdg, stream, n_inst, n_seq, graphs=1):
             "graphs": bool(graphs), "vs_sequential": vs_seq, "_check": check}
 
 
-SERVE_SHARE_QUANTUM = 262144.0  # DOF: a request of L DOF advances every round(L / quantum)-th tick (<= 16)
-SERVE_SHARE_MAX_STRIDE = 16
+SERVE_DOF_CAP = 16e6  # smallest-first run: space-time DOF the admitted requests may hold at once
 
 
 def _serving_leg(stdg, rates, n_req):
@@ -882,14 +881,16 @@ def _serving_leg(stdg, rates, n_req):
             svc.append(time.perf_counter() - t0)
             seq_status.append(st["status"])
             seq_u.append(c.get_state())
-    runs = [(str(r), r, 0.0) for r in rates] + [("%d_shared" % rates[len(rates) // 2], rates[len(rates) // 2],
-                                                    SERVE_SHARE_QUANTUM)]
+    # every rate with arrival-order admission, and one rate with smallest-first admission under a
+    # cap on the admitted space-time DOF (stdg_server_set_policy)
+    pol_rate = rates[min(2, len(rates) - 1)]
+    runs = [(str(r), r, 0, 0.0) for r in rates] + [("%d_smallest_first" % pol_rate, pol_rate, 1, SERVE_DOF_CAP)]
     first_res = None
     pct = lambda v, q: 1e3 * v[min(len(v) - 1, int(q * len(v)))] if v else None
-    for key, rate, quantum in runs:
+    for key, rate, order, cap in runs:
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
         with stdg.Server(2, stdg.EULER, max(64, n_req), arena) as srv:
-            srv.configure(share_quantum=quantum, share_max_stride=SERVE_SHARE_MAX_STRIDE)
+            srv.set_policy(order, cap)
             t0 = time.perf_counter()
             tickets = []
             for (d, u0, _), ta in zip(reqs, arrivals):
@@ -919,9 +920,9 @@ def _serving_leg(stdg, rates, n_req):
             "sequential_modelled": {"p50_ms": pct(seq_lat, 0.5), "p99_ms": pct(seq_lat, 0.99),
                                     "solves_per_s": len(seq_lat) / fin}}
     out["scheduling"] = {"graphs": True, "autotune": False,
-                         "size_aware_sharing": "off, except the '<rate>_shared' run: a request of L DOF advances "
-                                               "every round(L / %g)-th tick (at most %d)" %
-                                               (SERVE_SHARE_QUANTUM, SERVE_SHARE_MAX_STRIDE)}
+                         "admission": "arrival order by device memory, except the '<rate>_smallest_first' run: "
+                                      "the queued request with the fewest space-time DOF first, while the admitted "
+                                      "ones hold at most %g DOF" % SERVE_DOF_CAP}
     out["sequential_path"] = ("stdg_advance_slab per request (FP32 exact Jv, point-block preconditioner, "
                               "restarted GMRES); service times measured on the GPU, latencies modelled from them "
                               "under the same arrivals with one FIFO queue")
@@ -963,7 +964,8 @@ def _density_wave_leg(stdg, stream, slabs=2):
                        "(dt = %.6g), Newton rtol 1e-10, GMRES(30) forcing %g, %s initial guess" % (
                            dt, WORKLOAD["gmres_rtol"], "extrapolated" if WORKLOAD["predictor"] else "constant")}
     finals = {}
-    for name, prec, jv in (("fp64", stdg.FP64, stdg.JV_FD), ("mixed_fp32", stdg.MIXED_FP32, stdg.JV_EXACT)):
+    for name, prec, jv in (("fp64", stdg.FP64, stdg.JV_FD), ("mixed_fp32", stdg.MIXED_FP32, stdg.JV_EXACT),
+                           ("mixed_bf16", stdg.MIXED_BF16, stdg.JV_EXACT)):
         dd = stdg.make_config(**dict(base, dt=dt, precision=prec, jv_mode=jv))
         with stdg.Context(dd, stream.cuda_stream) as c:
             dof = c.slab_len
@@ -989,11 +991,16 @@ def _density_wave_leg(stdg, stream, slabs=2):
     out["rel_l2_mixed_vs_fp64"] = float(np.linalg.norm(finals["mixed_fp32"] - finals["fp64"]) /
                                         np.linalg.norm(finals["fp64"]))
     out["speedup_mixed"] = out["fp64"]["ms_per_slab"] / out["mixed_fp32"]["ms_per_slab"]
+    out["rel_l2_mixed_bf16_vs_fp64"] = float(np.linalg.norm(finals["mixed_bf16"] - finals["fp64"]) /
+                                             np.linalg.norm(finals["fp64"]))
+    out["mixed_bf16"]["what"] = ("as mixed_fp32, with the volume contractions of the exact Jacobian-vector "
+                                 "product on the tensor cores (tcgen05, BF16 inputs, FP32 accumulation)")
     # the same configuration on a reduced grid (K^3, same N, s, CFL, tolerances, guess), both
     # precisions, for the oracle check: the 32^3 grid is beyond the oracle's time budget
     Kr = WAVE3D_CHECK_K
     gpu = {}
-    for name, prec, jv in (("fp64", stdg.FP64, stdg.JV_FD), ("mixed_fp32", stdg.MIXED_FP32, stdg.JV_EXACT)):
+    for name, prec, jv in (("fp64", stdg.FP64, stdg.JV_FD), ("mixed_fp32", stdg.MIXED_FP32, stdg.JV_EXACT),
+                           ("mixed_bf16", stdg.MIXED_BF16, stdg.JV_EXACT)):
         dd = stdg.make_config(**dict(base, cells=[Kr, Kr, Kr], dt=1.0, precision=prec, jv_mode=jv))
         with stdg.Context(dd, stream.cuda_stream) as c:
             Xr = c.node_coordinates()
@@ -1081,8 +1088,8 @@ def main():
                     help="instances solved one at a time for the batched-vs-sequential comparison")
     ap.add_argument("--batch-graphs", type=int, choices=[0, 1], default=1,
                     help="0: the batched leg launches its kernels per tick instead of replaying a CUDA graph")
-    ap.add_argument("--serve-requests", type=int, default=24)
-    ap.add_argument("--serve-rates", default="100,1000,5000")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-rates", default="5,10,100,1000,5000")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
