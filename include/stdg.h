@@ -290,8 +290,10 @@ stdg_status stdg_slab_norm_noalloc(const double* x, size_t len, double* out, voi
  *   newton_maxit x ceil(gmres_maxit / gmres_m) such steps, the GMRES-iteration
  *   budget of the single-slab solver), right-
  *   preconditioned, with FP32 Krylov vectors and exact (forward-mode) FP32
- *   Jacobian-vector products; then u^{n+1} = U^s.  Preconditioner: Euler and
- *   inst->precond == STDG_PRECOND_POINT_BLOCK: the point-block P above;
+ *   Jacobian-vector products; then u^{n+1} = U^s.  Preconditioner: Euler with
+ *   inst->precond == STDG_PRECOND_POINT_BLOCK: the point-block P above; Euler
+ *   otherwise: the temporal-mass scaling diag(1 / omega_m) (the point block
+ *   stalls FGMRES on high-degree slabs with s = 2);
  *   scalar equations on grids whose element counts are powers of two (and
  *   whose lines fit 4096 values): the global inverse of
  *   C (x) I - dt/2 M_tau (x) (A_x (+) A_y), A_a the periodic 1D operator of the

@@ -873,6 +873,7 @@ stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* d, const doubl
   sb.dim = l.dim;
   sb.n = l.n;
   sb.kron = (d->equation != STDG_EULER && d->precond != STDG_PRECOND_POINT_BLOCK) ? 1 : 0;
+  sb.pbtm = (d->equation == STDG_EULER && d->precond != STDG_PRECOND_POINT_BLOCK) ? 1 : 0;
   sb.kdat = reinterpret_cast<const float*>(base + l.off_K);
   sb.fdm = 0;
   sb.fkx = l.kx;
