@@ -38,7 +38,6 @@ UNIT = "GDOF/s"
 WORKLOAD = dict(dim=2, cells=(64, 64), lo=(0.0, 0.0), hi=(10.0, 10.0), N=4, s=4, gamma=1.4, cfl=0.5,
                 newton_rtol=1e-10, gmres_m=30, gmres_rtol=0.05, predictor=1)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x FP64 FMA/clk/SM x flop/FMA x max SM clock
-HBM_PEAK_GBS = 6767.7
 
 
 def _workload_name():
@@ -759,11 +758,14 @@ def _vortex_requests(stdg, n, seed=7):
 
 def _sequential_config(stdg, d):
     """The plain one-solve-at-a-time GPU path at the same accuracy: a context with FP32 exact
-    Jacobian-vector products, FP64 Newton and the point-block preconditioner (restarted GMRES)."""
+    Jacobian-vector products, FP64 Newton and restarted GMRES, preconditioned by the point blocks
+    for the scalar (viscous) equations and by the temporal-mass scaling for Euler (the point
+    block stalls on high-degree Euler slabs with s = 2)."""
     import ctypes
     dm = stdg.stdg_config_desc()
     ctypes.memmove(ctypes.byref(dm), ctypes.byref(d), ctypes.sizeof(d))
-    dm.precision, dm.jv_mode, dm.precond, dm.gmres_maxit = stdg.MIXED_FP32, stdg.JV_EXACT, stdg.PRECOND_POINT_BLOCK, 600
+    pc = stdg.PRECOND_TEMPORAL_MASS if d.equation == stdg.EULER else stdg.PRECOND_POINT_BLOCK
+    dm.precision, dm.jv_mode, dm.precond, dm.gmres_maxit = stdg.MIXED_FP32, stdg.JV_EXACT, pc, 600
     return dm
 
 
@@ -794,9 +796,18 @@ def _batched_leg(stdg, stream, n_inst, n_seq, graphs=1):
     items = _burgers_instances(stdg, n_inst)
     free, _ = torch.cuda.mem_get_info()
     arena = int(free * 0.7)
+    # the same instances with the heuristic tile sizes (autotuning off), for comparison
     with stdg.Batch(2, stdg.BURGERS, n_inst, arena, stream.cuda_stream) as B:
-        if not graphs:
-            B.configure(use_graphs=False)  # plain launches per tick (for per-kernel profiling)
+        B.configure(use_graphs=bool(graphs), autotune=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out_h = _run_batch(stdg, B, items)
+        torch.cuda.synchronize()
+        T_heur = time.perf_counter() - t0
+    # the leg itself: tile sizes measured per (dim, N, s) class on a loaded virtual grid (the
+    # measurement, on first use of a class, is inside the timed region)
+    with stdg.Batch(2, stdg.BURGERS, n_inst, arena, stream.cuda_stream) as B:
+        B.configure(use_graphs=bool(graphs), autotune=True)  # graphs 0: plain launches (per-kernel profiling)
         need = sum(B.slot_bytes(d) for d, _, _ in items)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -849,7 +860,10 @@ def _batched_leg(stdg, stream, n_inst, n_seq, graphs=1):
             "counting": "instances_per_s and gdof_evals_per_s count the instances that converged (status 0)",
             "status_counts": {str(k): statuses.count(k) for k in sorted(set(statuses))},
             "gmres_its_mean": float(np.mean(its)), "gmres_its_max": int(max(its)),
-            "graphs": bool(graphs), "vs_sequential": vs_seq, "_check": check}
+            "graphs": bool(graphs), "autotune": True,
+            "heuristic_tiles": {"seconds": T_heur, "instances_per_s": [x[0] for x in out_h].count(0) / T_heur,
+                                "failed": n_inst - [x[0] for x in out_h].count(0)},
+            "vs_sequential": vs_seq, "_check": check}
 
 
 SERVE_DOF_CAP = 16e6  # smallest-first run: space-time DOF the admitted requests may hold at once
@@ -923,9 +937,9 @@ def _serving_leg(stdg, rates, n_req):
                          "admission": "arrival order by device memory, except the '<rate>_smallest_first' run: "
                                       "the queued request with the fewest space-time DOF first, while the admitted "
                                       "ones hold at most %g DOF" % SERVE_DOF_CAP}
-    out["sequential_path"] = ("stdg_advance_slab per request (FP32 exact Jv, point-block preconditioner, "
-                              "restarted GMRES); service times measured on the GPU, latencies modelled from them "
-                              "under the same arrivals with one FIFO queue")
+    out["sequential_path"] = ("stdg_advance_slab per request (FP32 exact Jv, temporal-mass scaling, restarted "
+                              "GMRES); service times measured on the GPU, latencies modelled from them under the "
+                              "same arrivals with one FIFO queue")
     out["sequential_statuses"] = {str(k): seq_status.count(k) for k in sorted(set(seq_status))}
     out["counting"] = "solves_per_s and the latency percentiles count the requests that converged (status 0)"
     # a seeded sample of requests small enough for the oracle, with the served and sequential results
@@ -979,6 +993,8 @@ def _density_wave_leg(stdg, stream, slabs=2):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
             finals[name] = c.get_state()
+            if name != "fp64":
+                out["roofline_" + name + "_jv"] = _jv32_roofline(stdg, c, dof, inputs, name)
             evals = sum(x["residual_evals"] + x["jv_evals"] for x in st)
             out[name] = {"ms_per_slab": ms / slabs, "gdof_evals_per_s": evals * dof / (ms * 1e-3) / 1e9,
                          "newton_its": [x["newton_its"] for x in st], "gmres_its": [x["gmres_its"] for x in st],
@@ -1017,6 +1033,46 @@ def _density_wave_leg(stdg, stream, slabs=2):
     out["_check"] = [{"kind": "wave3d", "K": Kr, "N": N, "s": s, "nslabs": WAVE3D_CHECK_SLABS,
                       "rtol": base["newton_rtol"], "eta": base["gmres_rtol"], "gpu": gpu}]
     return out
+
+
+def _hbm_peak():
+    """(GB/s, source): the measured copy bandwidth of this machine, else the fallback figure."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def _jv32_roofline(stdg, c, dof, inputs, name, reps=12):
+    """The FP32 exact Jacobian-vector kernel of the 3D leg alone (stdg_jv_fp32 on the final slab and
+    a random direction, L2 flushed by a 256 MB write before each launch, the library's per-launch
+    CUDA events): algorithmic bytes 12 per DOF (read U and v, write J v) / median launch time."""
+    import torch
+    U32 = torch.from_numpy(c.get_slab()).cuda().float()
+    v32 = torch.from_numpy(inputs.random_array(dof, 5)).cuda().float()
+    out = torch.empty_like(U32)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    c.profile_read(reset=True)
+    c.profile_enable(True)
+    ms = []
+    for i in range(reps):
+        flush.fill_(i & 255)
+        torch.cuda.synchronize()
+        c.jv_fp32(U32, v32, out)
+        pr = c.profile_read(reset=True)
+        ms.append(pr["jv"]["ms"] / max(1, pr["jv"]["launches"]))
+    c.profile_enable(False)
+    t = sorted(ms[2:])[len(ms[2:]) // 2]
+    peak, src = _hbm_peak()
+    gbs = 12.0 * dof / (t * 1e-3) / 1e9
+    prof = "jv_tangent32_euler3d_dw32.txt" if name == "mixed_fp32" else "jv_tangent_bf16_euler3d_dw32.txt"
+    return {"bound": "hbm", "kernel": "jv_tangent_kernel<3,4,3,%s> (%s exact J v)" % (
+                "1,false" if name == "mixed_fp32" else "2,true", "FP32" if name == "mixed_fp32" else "BF16 tensor-core"),
+            "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_source": src,
+            "avg_launch_ms": t, "algorithmic_bytes_per_launch": 12.0 * dof,
+            "traffic": _ncu_value(prof, "dram_bytes_per_launch")}
 
 
 WAVE3D_CHECK_K = 4
@@ -1060,18 +1116,23 @@ def _advection_leg(stdg, stream, slabs=100, reps=5):
             "_check": [{"kind": "advection1d", "nslabs": slabs, "gpu": {"fp64": u}}]}
 
 
-def _ncu_traffic():
-    """DRAM bytes per launch of the FD Jv kernel from the committed ncu summary, or None."""
-    p = os.path.join(ROOT, "profiles", "jv_fd_euler2d_vortex64.txt")
+def _ncu_value(fname, key):
+    """A 'key: value' figure from a committed ncu summary under profiles/, or None."""
+    p = os.path.join(ROOT, "profiles", fname)
     if not os.path.exists(p):
         return None
     for line in open(p):
-        if line.startswith("dram_bytes_per_launch:"):
+        if line.startswith(key + ":"):
             try:
                 return float(line.split(":", 1)[1].split()[0])
             except ValueError:
                 return None
     return None
+
+
+def _ncu_traffic():
+    """DRAM bytes per launch of the FD Jv kernel from the committed ncu summary, or None."""
+    return _ncu_value("jv_fd_euler2d_vortex64.txt", "dram_bytes_per_launch")
 
 
 def main():
@@ -1090,10 +1151,53 @@ def main():
                     help="0: the batched leg launches its kernels per tick instead of replaying a CUDA graph")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-rates", default="5,10,100,1000,5000")
+    ap.add_argument("--kernel", choices=["jv32", "jv_bf16"], default=None,
+                    help="only the 3D density-wave Jacobian-vector kernel (FP32 or BF16 tensor cores) on a "
+                         "K^3 grid with a one-row Krylov basis (a small device footprint for ncu captures)")
+    ap.add_argument("--kernel-grid", type=int, default=32)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.kernel:
+        return kernel_only(args)
     return gpu_arm(args)
+
+
+def kernel_only(args):
+    """The 3D density-wave Jacobian-vector kernel alone: --warmup + --steps launches, L2 flushed before
+    each, CUDA-event time per launch from the library's profiler; one JSON line (not the bench line)."""
+    import numpy as np
+    import torch
+    from paper_2201_05800_gb300 import build, inputs, stdg
+    _build_then_load(1, 0, build.build, stdg.load)
+    K = args.kernel_grid
+    prec = stdg.MIXED_BF16 if args.kernel == "jv_bf16" else stdg.MIXED_FP32
+    d = stdg.make_config(dim=3, cells=[K, K, K], lo=[0, 0, 0], hi=[1, 1, 1], N=3, s=3, equation=stdg.EULER,
+                         gamma=1.4, dt=0.5 / K / 2.6, gmres_m=1, jv_mode=stdg.JV_EXACT, precision=prec)
+    with stdg.Context(d) as c:
+        X = c.node_coordinates()
+        u0 = inputs.density_wave(X[:, 0], X[:, 1], X[:, 2]).ravel()
+        L = c.slab_len
+        U = torch.from_numpy(np.tile(u0.reshape(-1, 1, 64 * 5), (1, 3, 1)).ravel()).cuda()
+        U = (U * (1.0 + 1e-3 * torch.from_numpy(inputs.random_array(L, 21)).cuda())).float()
+        v = torch.from_numpy(inputs.random_array(L, 22)).cuda().float()
+        out = torch.empty_like(U)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        c.profile_enable(True)
+        ms = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(i & 255)
+            torch.cuda.synchronize()
+            c.profile_read(reset=True)
+            c.jv_fp32(U, v, out)
+            pr = c.profile_read(reset=True)
+            ms.append(pr["jv"]["ms"] / max(1, pr["jv"]["launches"]))
+        t = sorted(ms[args.warmup:])[len(ms[args.warmup:]) // 2]
+        peak, src = _hbm_peak()
+        print(json.dumps({"kernel": args.kernel, "grid": K, "dof": int(L), "launch_ms_median": t,
+                          "algorithmic_bytes": 12.0 * L, "gbs": 12.0 * L / (t * 1e-3) / 1e9,
+                          "frac_hbm": 12.0 * L / (t * 1e-3) / 1e9 / peak, "peak_gbs": peak, "peak_source": src}))
+    return 0
 
 
 if __name__ == "__main__":
