@@ -21,7 +21,10 @@ using namespace stdg;
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kChunkValues = 16384;   // values per work item of the build / dot / update kernels
+// values per work item of the build / dot / update kernels: a power of two in [kChunkMin, kChunkMax]
+// near L / (2 SMs), so that a slot alone spreads over the whole GPU and a large one keeps few
+// partial sums (it depends on the slot and the device only, not on the other slots)
+constexpr size_t kChunkMin = 2048, kChunkMax = 16384;
 constexpr size_t kOpSmemCap = 96 * 1024;
 constexpr size_t kFdmMaxLine = 4096;  // complex values of one x-line group or one y column of the fdm passes
 
@@ -215,7 +218,8 @@ Layout layout_of(const stdg_config_desc* d) {
   }
   l.S = (size_t)l.nelem * l.nd * l.r;
   l.L = l.S * l.s;
-  l.npinv = (size_t)l.nelem * l.nd * l.s * l.s;
+  // the s x s blocks per spatial node exist only for the point-block preconditioner
+  l.npinv = d->precond == STDG_PRECOND_POINT_BLOCK ? (size_t)l.nelem * l.nd * l.s * l.s : 0;
   size_t o = 0;
   l.off_U = o;
   o += align_up(l.L * 8);
@@ -867,7 +871,9 @@ stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* d, const doubl
   sb.nd = l.nd;
   sb.r = l.r;
   sb.L = l.L;
-  sb.chunk_elems = std::max(1, (int)(kChunkValues / ((size_t)l.s * l.nd * l.r)));
+  size_t chunk = kChunkMin;
+  while (chunk < kChunkMax && chunk < l.L / (2 * (size_t)b->sms)) chunk <<= 1;
+  sb.chunk_elems = std::max(1, (int)(chunk / ((size_t)l.s * l.nd * l.r)));
   sb.nitems = (int)((l.nelem + sb.chunk_elems - 1) / sb.chunk_elems);
   sb.item0 = 0;
   sb.dim = l.dim;

@@ -58,7 +58,7 @@ struct SlotBuf {
   // element tensor-product preconditioner (scalar equations; kron = 1), see eng_kron_kernel:
   // kdat = [Vx^-1 | Vx | Vy^-1 | Vy] (n x n each) then P_k^-1 (s x s) per mode k of the element
   int kron, dim, n;
-  int pbtm;  // Euler slots without STDG_PRECOND_POINT_BLOCK: the block array holds diag(1 / omega_m)
+  int pbtm;  // Euler slots without STDG_PRECOND_POINT_BLOCK: z = diag(1 / omega_m) v (no block array)
   const float* kdat;
   // global fast-diagonalisation preconditioner (scalar slots on periodic grids whose element
   // counts are powers of two; fdm = 1 replaces kron), see engine_fdm.cu:

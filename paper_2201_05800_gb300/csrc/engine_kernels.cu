@@ -9,12 +9,6 @@ namespace stdg {
 
 namespace {
 
-__device__ __forceinline__ double warp_sum_xor(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // element range of a chunk item
 __device__ __forceinline__ void chunk_range(const SlotBuf& b, int idx, long long* e0, long long* e1) {
   *e0 = (long long)idx * b.chunk_elems;
@@ -186,12 +180,21 @@ __global__ void __launch_bounds__(kEngThreads) eng_control_kernel(const __grid_c
     if (lane == 0) c.upd = kUpdNone;
     return;
   }
+  // lane i sums row i over the slot's work items in a fixed order (four interleaved partial
+  // sums, combined as (s0 + s1) + (s2 + s3)); rows are consecutive in memory per item
   const int k = ph == kPhResid ? 1 : c.j + 2;
-  for (int i = 0; i < k; ++i) {
-    double p = 0.0;
-    for (int q = lane; q < b.nitems; q += 32) p += L.partials[(size_t)(b.item0 + q) * kEngRows + i];
-    p = warp_sum_xor(p);
-    if (lane == 0) sp[wid][i] = p;
+  if (lane < k) {
+    const double* pp = L.partials + (size_t)b.item0 * kEngRows + lane;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int q = 0;
+    for (; q + 4 <= b.nitems; q += 4) {
+      s0 += pp[(size_t)q * kEngRows];
+      s1 += pp[(size_t)(q + 1) * kEngRows];
+      s2 += pp[(size_t)(q + 2) * kEngRows];
+      s3 += pp[(size_t)(q + 3) * kEngRows];
+    }
+    for (; q < b.nitems; ++q) s0 += pp[(size_t)q * kEngRows];
+    sp[wid][lane] = (s0 + s1) + (s2 + s3);
   }
   __syncwarp();
   if (lane != 0) return;
@@ -350,7 +353,10 @@ __global__ void __launch_bounds__(kEngThreads) eng_update_kernel(const __grid_co
       } else if (mode == kUpdExtract) {
         b.uprev[e * tnode + q] = b.U[base + (size_t)(s - 1) * tnode];
       }
-      if (apply_z && !b.kron && !b.fdm) {  // Kron / fdm slots: z is formed by their own kernels
+      if (apply_z && b.pbtm) {  // temporal-mass scaling: z_m = x_m / omega_m
+        const OpArgs<float>& a = L.a32[item.slot];
+        for (int m = 0; m < s; ++m) zout[base + (size_t)m * tnode] = x[m] * a.inv_omega[m];
+      } else if (apply_z && !b.kron && !b.fdm) {  // Kron / fdm slots: z is formed by their own kernels
         const float* P = b.Pinv + (e * s * s) * nd + node;
         for (int m = 0; m < s; ++m) {
           float z = 0.f;

@@ -51,17 +51,7 @@ __global__ void __launch_bounds__(128) eng_build_kernel(const __grid_constant__ 
     if (!eng_runs(L, b) || b.kron || b.fdm) continue;
     const long long e0 = (long long)item.idx * b.chunk_elems;
     const long long e1 = e0 + b.chunk_elems < b.nelem ? e0 + b.chunk_elems : b.nelem;
-    if (b.pbtm) {  // temporal-mass scaling: P^-1 = diag(1 / omega_m) at every spatial node
-      const OpArgs<float>& a = L.a32[item.slot];
-      for (long long idx = e0 * b.nd + threadIdx.x; idx < e1 * b.nd; idx += blockDim.x) {
-        const long long e = idx / b.nd;
-        const int node = (int)(idx - e * b.nd);
-        for (int m = 0; m < b.s; ++m)
-          for (int j = 0; j < b.s; ++j)
-            b.Pinv[((size_t)e * b.s * b.s + m * b.s + j) * b.nd + node] = m == j ? a.inv_omega[m] : 0.f;
-      }
-      continue;
-    }
+    if (b.pbtm) continue;  // temporal-mass scaling: applied directly by the update kernel
     for (long long idx = e0 * b.nd + threadIdx.x; idx < e1 * b.nd; idx += blockDim.x)
       pb_build_node<DIM, EQ, float, float>(L.a32[item.slot], b.U, b.Pinv, idx);
   }
