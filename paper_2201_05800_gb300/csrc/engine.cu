@@ -325,6 +325,8 @@ stdg_status rebuild(stdg_batch* b) {
     const long long tiles = (l.nelem + hs.epb64 - 1) / hs.epb64;
     const long long tiles32 = (l.nelem + hs.epb32 - 1) / hs.epb32;
     // one item list serves both op kernels: tile indices valid for both epb values
+    hs.buf.op0 = (int)op.size();
+    hs.buf.nop = (int)std::max(tiles, tiles32);
     for (long long t = 0; t < std::max(tiles, tiles32); ++t) op.push_back({id, (int)t});
     hs.buf.item0 = (int)ch.size();
     for (int c = 0; c < hs.buf.nitems; ++c) ch.push_back({id, c});
@@ -876,6 +878,8 @@ stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* d, const doubl
   sb.chunk_elems = std::max(1, (int)(chunk / ((size_t)l.s * l.nd * l.r)));
   sb.nitems = (int)((l.nelem + sb.chunk_elems - 1) / sb.chunk_elems);
   sb.item0 = 0;
+  sb.op0 = sb.nop = 0;
+  sb.vec4 = l.L % 4 == 0 ? 1 : 0;
   sb.dim = l.dim;
   sb.n = l.n;
   sb.kron = (d->equation != STDG_EULER && d->precond != STDG_PRECOND_POINT_BLOCK) ? 1 : 0;

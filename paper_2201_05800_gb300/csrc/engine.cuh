@@ -54,6 +54,8 @@ struct SlotBuf {
   int chunk_elems;  // elements per work item of the build / dot / update kernels
   size_t L;         // slab length nelem * s * nd * r
   int item0, nitems;  // this slot's work items in the chunk list (control reduction)
+  int op0, nop;       // this slot's tiles in the operator item list (skipped together)
+  int vec4;           // L % 4 == 0: every row starts on 16 bytes (vector loads in dot / update)
   int stride, offset; // the slot takes part in tick t when (t + offset) % stride == 0
   // element tensor-product preconditioner (scalar equations; kron = 1), see eng_kron_kernel:
   // kdat = [Vx^-1 | Vx | Vy^-1 | Vy] (n x n each) then P_k^-1 (s x s) per mode k of the element

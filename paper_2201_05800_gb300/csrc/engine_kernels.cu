@@ -40,33 +40,41 @@ __device__ __forceinline__ void block_reduce_store(const double (&accd)[KB], int
 }
 
 // V_i . w over [v0, v1) for i < k, in passes over groups of 8 rows (few registers, so many
-// blocks stay resident; w is re-read from L1/L2 once per group), two values per thread and
-// iteration.  Per-warp sums of each row go to red[warp][row]; then one fixed-order sum.
+// blocks stay resident; w is re-read from L1/L2 once per group).  When the rows start on
+// 16 bytes the aligned body of the range is read in 16-byte words (four values per load),
+// the at most three values before and after it one by one.  Per-warp sums of each row go to
+// red[warp][row]; then one fixed-order sum.
 __device__ __forceinline__ void dot_rows(const SlotBuf& b, size_t v0, size_t v1, int j, int k,
                                          double (*red)[kEngRows], double* out) {
   constexpr int G = 8;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const float* w = b.V + (size_t)(j + 1) * b.L;
+  size_t a0 = v0, a1 = v0;  // 16-byte body [a0, a1)
+  if (b.vec4) {
+    a0 = (v0 + 3) & ~(size_t)3;
+    if (a0 > v1) a0 = v1;
+    a1 = a0 + ((v1 - a0) & ~(size_t)3);
+  }
   for (int g0 = 0; g0 < k; g0 += G) {
     float acc[G];
 #pragma unroll
     for (int i = 0; i < G; ++i) acc[i] = 0.f;
-    const size_t step = (size_t)2 * blockDim.x;
-    size_t v = v0 + threadIdx.x;
-    for (; v + blockDim.x < v1; v += step) {
-      const float w0 = w[v], w1 = w[v + blockDim.x];
+    const float4* w4 = reinterpret_cast<const float4*>(w);
+    for (size_t q = a0 / 4 + threadIdx.x; q < a1 / 4; q += blockDim.x) {
+      const float4 wv = w4[q];
 #pragma unroll
       for (int i = 0; i < G; ++i)
         if (g0 + i < k) {
-          const float* Vi = b.V + (size_t)(g0 + i) * b.L;
-          acc[i] = fmaf(Vi[v + blockDim.x], w1, fmaf(Vi[v], w0, acc[i]));
+          const float4 x = reinterpret_cast<const float4*>(b.V + (size_t)(g0 + i) * b.L)[q];
+          acc[i] = fmaf(x.w, wv.w, fmaf(x.z, wv.z, fmaf(x.y, wv.y, fmaf(x.x, wv.x, acc[i]))));
         }
     }
-    if (v < v1) {
-      const float w0 = w[v];
+    for (size_t v = threadIdx.x; v < (a0 - v0) + (v1 - a1); v += blockDim.x) {  // head, then tail
+      const size_t vv = v < a0 - v0 ? v0 + v : a1 + (v - (a0 - v0));
+      const float w0 = w[vv];
 #pragma unroll
       for (int i = 0; i < G; ++i)
-        if (g0 + i < k) acc[i] = fmaf(b.V[(size_t)(g0 + i) * b.L + v], w0, acc[i]);
+        if (g0 + i < k) acc[i] = fmaf(b.V[(size_t)(g0 + i) * b.L + vv], w0, acc[i]);
     }
     // warp sums of the group's rows by a reduce-scatter (rows past k are zeros)
     double d[G];
@@ -113,160 +121,210 @@ __global__ void __launch_bounds__(kEngThreads, 4) eng_dot_kernel(const __grid_co
   }
 }
 
-// Givens column update and the end-of-cycle test (lane 0 of the slot's warp).
-__device__ void finish_column(SlotCtl& c, const SlotBuf& b, OpArgs<float>& a32, double r2) {
+// Shared-memory copy of what the controller of one slot touches in a tick.
+struct CtlShared {
+  double red[kEngThreads / 32][kEngRows];  // per-warp sums of each row
+  double P[kEngRows];                      // the tick's reduced dot products
+  double h[kEngRows + 1];                  // column j of H
+  double cs[kEngRows], sn[kEngRows], sig[kEngRows + 1];
+  double g[kEngRows + 1], y[kEngRows];
+  double T[kEngRows * kEngRows];  // leading kd x kd block of H at the end of a cycle
+  int kd;                         // > 0 when the cycle ended (the triangular solve follows)
+};
+
+// Givens column update and the end-of-cycle test (thread 0): column j of H in S.h, the
+// earlier rotations in S.cs / S.sn.  Returns the number of basis vectors of the
+// correction when the cycle ends, else 0.
+__device__ int finish_column(SlotCtl& c, const SlotBuf& b, OpArgs<float>& a32, double r2, CtlShared& S) {
   const int j = c.j;
   if (!isfinite(r2)) {
     c.status = STDG_ERR_NAN;
     c.phase = kPhDone;
     c.upd = kUpdNone;
-    return;
+    return 0;
   }
   const double hn = sqrt(r2 > 0.0 ? r2 : 0.0);
-  double* H = c.H;
+  double* h = S.h;
   for (int i = 0; i < j; ++i) {
-    const double t0 = c.cs[i] * H[i * kEngRows + j] + c.sn[i] * H[(i + 1) * kEngRows + j];
-    H[(i + 1) * kEngRows + j] = -c.sn[i] * H[i * kEngRows + j] + c.cs[i] * H[(i + 1) * kEngRows + j];
-    H[i * kEngRows + j] = t0;
+    const double t0 = S.cs[i] * h[i] + S.sn[i] * h[i + 1];
+    h[i + 1] = -S.sn[i] * h[i] + S.cs[i] * h[i + 1];
+    h[i] = t0;
   }
-  double den = hypot(H[j * kEngRows + j], hn);
+  double den = hypot(h[j], hn);
   if (den == 0.0) den = 1e-300;
-  c.cs[j] = H[j * kEngRows + j] / den;
-  c.sn[j] = hn / den;
-  H[j * kEngRows + j] = den;
-  c.g[j + 1] = -c.sn[j] * c.g[j];
-  c.g[j] = c.cs[j] * c.g[j];
+  const double csj = h[j] / den, snj = hn / den;
+  h[j] = den;
+  c.cs[j] = csj;
+  c.sn[j] = snj;
+  for (int i = 0; i <= j; ++i) c.H[i * kEngRows + j] = h[i];
+  const double gj = c.g[j];
+  const double gj1 = -snj * gj;
+  c.g[j + 1] = gj1;
+  c.g[j] = csj * gj;
   c.gmres_its += 1;
   c.sig[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
-  const bool done = fabs(c.g[j + 1]) <= c.tol || j + 1 >= c.m || hn <= 1e-300 * c.beta;
+  const bool done = fabs(gj1) <= c.tol || j + 1 >= c.m || hn <= 1e-300 * c.beta;
   if (done) {
-    // y = H^-1 g (upper triangular), U += sum_i y_i z_i
-    const int kd = j + 1;
-    double y[kEngRows];
-    for (int i = kd - 1; i >= 0; --i) {
-      double acc = c.g[i];
-      for (int q = i + 1; q < kd; ++q) acc -= H[i * kEngRows + q] * y[q];
-      y[i] = acc / H[i * kEngRows + i];
-    }
-    for (int i = 0; i < kd; ++i) c.coef[i] = y[i];
     c.upd = kUpdSolve;
-    c.upd_k = kd;
+    c.upd_k = j + 1;
     c.newton_its += 1;
     c.phase = kPhResid;
-  } else {
-    // w -= V c (coefficients of this pass), z_{j+1} = P^-1 (w / |w|)
-    c.upd = kUpdGSZ;
-    c.upd_row = j + 1;
-    c.upd_k = j + 1;
-    c.zscale = c.sig[j + 1];
-    c.j = j + 1;
-    c.phase = kPhArnoldi;
-    a32.v = b.Z + (size_t)(j + 1) * b.L;
-    a32.out = b.V + (size_t)(j + 2) * b.L;
+    return j + 1;
   }
+  // w -= V c (coefficients of this pass), z_{j+1} = P^-1 (w / |w|)
+  c.upd = kUpdGSZ;
+  c.upd_row = j + 1;
+  c.upd_k = j + 1;
+  c.zscale = c.sig[j + 1];
+  c.j = j + 1;
+  c.phase = kPhArnoldi;
+  a32.v = b.Z + (size_t)(j + 1) * b.L;
+  a32.out = b.V + (size_t)(j + 2) * b.L;
+  return 0;
 }
 
-// One warp per active slot.
+// One block per active slot (grid = number of active slots).  The block reduces the
+// slot's per-item partial sums: warp w takes the groups of kA consecutive items
+// w, w + W, w + 2W, ... (kA loads in flight per lane, lane = row), each warp combines its
+// kA running sums in a fixed tree and the warps' sums are added in warp order, so the
+// result does not depend on timing.  Thread 0 then runs the Newton / Arnoldi logic on a
+// shared-memory copy of the Givens data; at the end of a cycle the block stages H's
+// leading block for the triangular solve.
 __global__ void __launch_bounds__(kEngThreads) eng_control_kernel(const __grid_constant__ EngLaunch L) {
-  __shared__ double sp[kEngThreads / 32][kEngRows];
+  constexpr int W = kEngThreads / 32, kA = 8;
+  __shared__ CtlShared S;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (g >= L.n_active) return;
-  const int slot = L.active[g];
+  const int slot = L.active[blockIdx.x];
   SlotCtl& c = L.ctl[slot];
   const SlotBuf& b = L.buf[slot];
   const int ph = c.phase;
   if ((ph != kPhResid && ph != kPhArnoldi && ph != kPhReorth) || !eng_runs(L, b)) {
-    if (lane == 0) c.upd = kUpdNone;
+    if (threadIdx.x == 0) c.upd = kUpdNone;
     return;
   }
-  // lane i sums row i over the slot's work items in a fixed order (four interleaved partial
-  // sums, combined as (s0 + s1) + (s2 + s3)); rows are consecutive in memory per item
   const int k = ph == kPhResid ? 1 : c.j + 2;
+  const int j = c.j;
   if (lane < k) {
     const double* pp = L.partials + (size_t)b.item0 * kEngRows + lane;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int q = 0;
-    for (; q + 4 <= b.nitems; q += 4) {
-      s0 += pp[(size_t)q * kEngRows];
-      s1 += pp[(size_t)(q + 1) * kEngRows];
-      s2 += pp[(size_t)(q + 2) * kEngRows];
-      s3 += pp[(size_t)(q + 3) * kEngRows];
+    const int nit = b.nitems;
+    double acc[kA];
+#pragma unroll
+    for (int a = 0; a < kA; ++a) acc[a] = 0.0;
+    int q0 = wid * kA;
+    for (; q0 + kA <= nit; q0 += W * kA) {
+#pragma unroll
+      for (int a = 0; a < kA; ++a) acc[a] += pp[(size_t)(q0 + a) * kEngRows];
     }
-    for (; q < b.nitems; ++q) s0 += pp[(size_t)q * kEngRows];
-    sp[wid][lane] = (s0 + s1) + (s2 + s3);
+#pragma unroll
+    for (int a = 0; a < kA; ++a)
+      if (q0 + a < nit) acc[a] += pp[(size_t)(q0 + a) * kEngRows];
+    S.red[wid][lane] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
   }
-  __syncwarp();
-  if (lane != 0) return;
-  const double* P = sp[wid];
-  OpArgs<float>& a32 = L.a32[slot];
-  if (ph == kPhResid) {
-    const double res = sqrt(P[0]);
-    c.resid_evals += 1;
-    c.res = res;
-    if (c.resid_evals == 1) {
-      c.res0 = res;
-      c.target = fmax(c.rtol * res, c.atol);
+  if (ph != kPhResid) {
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+      S.cs[i] = c.cs[i];
+      S.sn[i] = c.sn[i];
     }
-    if (!isfinite(res)) {
-      c.status = STDG_ERR_NAN;
-      c.phase = kPhDone;
-      c.upd = kUpdNone;
-    } else if (res <= c.target) {
-      c.status = STDG_OK;
-      c.phase = kPhDone;
-      c.upd = kUpdExtract;
-    } else if (c.newton_its >= c.newton_maxit) {
-      c.status = STDG_ERR_NOT_CONVERGED;
-      c.phase = kPhDone;
-      c.upd = kUpdExtract;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+      S.sig[i] = c.sig[i];
+      if (ph == kPhReorth) S.h[i] = c.H[i * kEngRows + j];
+    }
+  }
+  if (threadIdx.x == 0) S.kd = 0;
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double d = 0.0;
+    for (int q = 0; q < W; ++q) d += S.red[q][threadIdx.x];
+    S.P[threadIdx.x] = d;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double* P = S.P;
+    OpArgs<float>& a32 = L.a32[slot];
+    if (ph == kPhResid) {
+      const double res = sqrt(P[0]);
+      c.resid_evals += 1;
+      c.res = res;
+      if (c.resid_evals == 1) {
+        c.res0 = res;
+        c.target = fmax(c.rtol * res, c.atol);
+      }
+      if (!isfinite(res)) {
+        c.status = STDG_ERR_NAN;
+        c.phase = kPhDone;
+        c.upd = kUpdNone;
+      } else if (res <= c.target) {
+        c.status = STDG_OK;
+        c.phase = kPhDone;
+        c.upd = kUpdExtract;
+      } else if (c.newton_its >= c.newton_maxit) {
+        c.status = STDG_ERR_NOT_CONVERGED;
+        c.phase = kPhDone;
+        c.upd = kUpdExtract;
+      } else {
+        c.beta = res;
+        c.tol = c.gmres_rtol * res;
+        c.sig[0] = -1.0 / res;  // V_0 holds R, v_0 = -R / |R|
+        for (int i = 0; i <= kEngRows; ++i) c.g[i] = 0.0;
+        c.g[0] = res;
+        c.j = 0;
+        c.upd = kUpdInit;
+        c.zscale = c.sig[0];
+        c.phase = kPhArnoldi;
+        a32.v = b.Z;
+        a32.out = b.V + b.L;
+      }
+    } else if (ph == kPhArnoldi) {
+      c.jv_evals += 1;
+      const double w2 = P[j + 1];
+      double h2 = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        const double h = S.sig[i] * P[i];
+        S.h[i] = h;
+        h2 += h * h;
+        c.coef[i] = S.sig[i] * h;
+      }
+      const double r2 = w2 - h2;
+      if (!(r2 > 0.01 * w2) && isfinite(r2)) {
+        // strong cancellation: apply this projection, then project once more
+        for (int i = 0; i <= j; ++i) c.H[i * kEngRows + j] = S.h[i];
+        c.phase = kPhReorth;
+        c.upd = kUpdGS;
+        c.upd_row = j + 1;
+        c.upd_k = j + 1;
+      } else {
+        S.kd = finish_column(c, b, a32, r2, S);
+      }
     } else {
-      c.beta = res;
-      c.tol = c.gmres_rtol * res;
-      c.sig[0] = -1.0 / res;  // V_0 holds R, v_0 = -R / |R|
-      for (int i = 0; i <= kEngRows; ++i) c.g[i] = 0.0;
-      c.g[0] = res;
-      c.j = 0;
-      c.upd = kUpdInit;
-      c.zscale = c.sig[0];
-      c.phase = kPhArnoldi;
-      a32.v = b.Z;
-      a32.out = b.V + b.L;
+      double e2 = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        const double h = S.sig[i] * P[i];
+        S.h[i] += h;
+        e2 += h * h;
+        c.coef[i] = S.sig[i] * h;
+      }
+      S.kd = finish_column(c, b, a32, P[j + 1] - e2, S);
     }
-    return;
   }
-  const int j = c.j;
-  double* H = c.H;
-  if (ph == kPhArnoldi) {
-    c.jv_evals += 1;
-    const double w2 = P[j + 1];
-    double h2 = 0.0;
-    for (int i = 0; i <= j; ++i) {
-      const double h = c.sig[i] * P[i];
-      H[i * kEngRows + j] = h;
-      h2 += h * h;
-      c.coef[i] = c.sig[i] * h;
-    }
-    const double r2 = w2 - h2;
-    if (!(r2 > 0.01 * w2) && isfinite(r2)) {
-      // strong cancellation: apply this projection, then project once more
-      c.phase = kPhReorth;
-      c.upd = kUpdGS;
-      c.upd_row = j + 1;
-      c.upd_k = j + 1;
-      return;
-    }
-    finish_column(c, b, a32, r2);
-  } else {
-    double e2 = 0.0;
-    for (int i = 0; i <= j; ++i) {
-      const double h = c.sig[i] * P[i];
-      H[i * kEngRows + j] += h;
-      e2 += h * h;
-      c.coef[i] = c.sig[i] * h;
-    }
-    finish_column(c, b, a32, P[j + 1] - e2);
+  __syncthreads();
+  const int kd = S.kd;
+  if (kd == 0) return;
+  // end of the cycle: y = H^-1 g (upper triangular), the update is U += sum_i y_i z_i
+  for (int t = threadIdx.x; t < kd * kd; t += blockDim.x) {
+    const int i = t / kd, q = t % kd;
+    if (q >= i) S.T[i * kEngRows + q] = q == kd - 1 ? S.h[i] : c.H[i * kEngRows + q];
   }
+  for (int i = threadIdx.x; i < kd; i += blockDim.x) S.g[i] = c.g[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = kd - 1; i >= 0; --i) {
+      double acc = S.g[i];
+      for (int q = i + 1; q < kd; ++q) acc -= S.T[i * kEngRows + q] * S.y[q];
+      S.y[i] = acc / S.T[i * kEngRows + i];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kd; i += blockDim.x) c.coef[i] = S.y[i];
 }
 
 // sum_{i<k} c_i X[i * ld] with four independent partial sums (loads of four rows in
@@ -293,9 +351,112 @@ __device__ __forceinline__ float rows_sum(const float* c, const float* X, size_t
   return (s0 + s1) + (s2 + s3);
 }
 
-// Vector update of one tick.  Thread per (element, value q of a temporal
-// node's block) of the chunk; the s temporal values of q are handled together
-// so that z = (P^-1 (x) I_r) x is formed in registers.
+// rows_sum for four consecutive values (16-byte loads of each row), the same association per value.
+__device__ __forceinline__ float4 rows_sum4(const float* c, const float* X, size_t ld, int k) {
+  float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
+  auto f4 = [&](int i) { return *reinterpret_cast<const float4*>(X + (size_t)i * ld); };
+  auto acc = [](float4& s, float ci, const float4& x) {
+    s.x = fmaf(ci, x.x, s.x);
+    s.y = fmaf(ci, x.y, s.y);
+    s.z = fmaf(ci, x.z, s.z);
+    s.w = fmaf(ci, x.w, s.w);
+  };
+  int i = 0;
+  for (; i + 8 <= k; i += 8) {
+    const float4 x0 = f4(i), x1 = f4(i + 1), x2 = f4(i + 2), x3 = f4(i + 3), x4 = f4(i + 4), x5 = f4(i + 5),
+                 x6 = f4(i + 6), x7 = f4(i + 7);
+    acc(s0, c[i], x0);
+    acc(s0, c[i + 4], x4);
+    acc(s1, c[i + 1], x1);
+    acc(s1, c[i + 5], x5);
+    acc(s2, c[i + 2], x2);
+    acc(s2, c[i + 6], x6);
+    acc(s3, c[i + 3], x3);
+    acc(s3, c[i + 7], x7);
+  }
+  for (; i + 4 <= k; i += 4) {
+    acc(s0, c[i], f4(i));
+    acc(s1, c[i + 1], f4(i + 1));
+    acc(s2, c[i + 2], f4(i + 2));
+    acc(s3, c[i + 3], f4(i + 3));
+  }
+  for (; i < k; ++i) acc(s0, c[i], f4(i));
+  return make_float4((s0.x + s1.x) + (s2.x + s3.x), (s0.y + s1.y) + (s2.y + s3.y), (s0.z + s1.z) + (s2.z + s3.z),
+                     (s0.w + s1.w) + (s2.w + s3.w));
+}
+
+// Updates that need no per-node s x s block (Init, GS, GSZ of slots without point blocks, and the
+// Newton update): value by value over the chunk's range [v0, v1), in 16-byte words over the
+// aligned body when the rows start on 16 bytes (and, with the temporal-mass scaling, each word
+// lies in one temporal node: nd r % 4 == 0).  z_m = zscale x_m / omega_m for temporal-mass slots.
+__device__ __forceinline__ void linear_update(const EngLaunch& L, const SlotBuf& b, int slot, int mode, int k,
+                                              int row, float zs, const float* cf, long long e0, long long e1) {
+  const int tnode = b.nd * b.r;
+  const size_t blockvals = (size_t)b.s * tnode;
+  const size_t v0 = (size_t)e0 * blockvals, v1 = (size_t)e1 * blockvals;
+  const bool scale = b.pbtm && (mode == kUpdInit || mode == kUpdGSZ);
+  const float* iw = L.a32[slot].inv_omega;
+  float* w = mode == kUpdInit ? b.V : b.V + (size_t)row * b.L;
+  float* z = mode == kUpdInit ? b.Z : b.Z + (size_t)row * b.L;
+  const bool vec = b.vec4 && (!scale || tnode % 4 == 0);
+  size_t a0 = v0, a1 = v0;
+  if (vec) {
+    a0 = (v0 + 3) & ~(size_t)3;
+    if (a0 > v1) a0 = v1;
+    a1 = a0 + ((v1 - a0) & ~(size_t)3);
+  }
+  // temporal node of value v (v0 starts an element block; a chunk holds at most a few thousand values)
+  auto tnode_of = [&](size_t v) { return ((int)(v - v0) / tnode) % b.s; };
+  for (size_t q = a0 / 4 + threadIdx.x; q < a1 / 4; q += blockDim.x) {
+    const size_t v = 4 * q;
+    if (mode == kUpdSolve) {
+      const float4 acc = rows_sum4(cf, b.Z + v, b.L, k);
+      double2* U2 = reinterpret_cast<double2*>(b.U + v);
+      double2 u01 = U2[0], u23 = U2[1];
+      u01.x += (double)acc.x;
+      u01.y += (double)acc.y;
+      u23.x += (double)acc.z;
+      u23.y += (double)acc.w;
+      U2[0] = u01;
+      U2[1] = u23;
+      *reinterpret_cast<float4*>(b.U32 + v) = make_float4((float)u01.x, (float)u01.y, (float)u23.x, (float)u23.y);
+      continue;
+    }
+    float4 x;
+    if (mode == kUpdInit) {
+      const double2* R2 = reinterpret_cast<const double2*>(b.R + v);
+      const double2 r01 = R2[0], r23 = R2[1];
+      x = make_float4((float)r01.x, (float)r01.y, (float)r23.x, (float)r23.y);
+    } else {
+      const float4 acc = rows_sum4(cf, b.V + v, b.L, k);
+      const float4 wv = *reinterpret_cast<const float4*>(w + v);
+      x = make_float4(wv.x - acc.x, wv.y - acc.y, wv.z - acc.z, wv.w - acc.w);
+    }
+    *reinterpret_cast<float4*>(w + v) = x;
+    if (scale) {
+      const float f = iw[tnode_of(v)];
+      *reinterpret_cast<float4*>(z + v) =
+          make_float4(zs * x.x * f, zs * x.y * f, zs * x.z * f, zs * x.w * f);
+    }
+  }
+  for (size_t t = threadIdx.x; t < (a0 - v0) + (v1 - a1); t += blockDim.x) {  // head, then tail
+    const size_t v = t < a0 - v0 ? v0 + t : a1 + (t - (a0 - v0));
+    if (mode == kUpdSolve) {
+      const double u = b.U[v] + (double)rows_sum(cf, b.Z + v, b.L, k);
+      b.U[v] = u;
+      b.U32[v] = (float)u;
+      continue;
+    }
+    const float x = mode == kUpdInit ? (float)b.R[v] : w[v] - rows_sum(cf, b.V + v, b.L, k);
+    w[v] = x;
+    if (scale) z[v] = zs * x * iw[tnode_of(v)];
+  }
+}
+
+// Vector update of one tick.  Point-block slots (Init, GSZ) and the extraction of u^{n+1}:
+// thread per (element, value q of a temporal node's block) of the chunk; the s temporal values
+// of q are handled together so that z = (P^-1 (x) I_r) x is formed in registers.  Everything
+// else: linear_update.
 __global__ void __launch_bounds__(kEngThreads) eng_update_kernel(const __grid_constant__ EngLaunch L) {
   __shared__ float cf[kEngRows];
   const int n = *L.n_chunk_items;
@@ -313,26 +474,34 @@ __global__ void __launch_bounds__(kEngThreads) eng_update_kernel(const __grid_co
     const float zs = (float)c.zscale;
     long long e0, e1;
     chunk_range(b, item.idx, &e0, &e1);
+    const bool pb_apply = (mode == kUpdInit || mode == kUpdGSZ) && !b.pbtm && !b.kron && !b.fdm;
+    if (mode != kUpdExtract && !pb_apply) {
+      linear_update(L, b, item.slot, mode, k, row, zs, cf, e0, e1);
+      __syncthreads();
+      continue;
+    }
     const int s = b.s, nd = b.nd, r = b.r;
     const int tnode = nd * r;
-    const size_t total = (size_t)(e1 - e0) * tnode;
-    for (size_t t = threadIdx.x; t < total; t += blockDim.x) {
+    const int total = (int)(e1 - e0) * tnode;  // a chunk holds at most a few thousand values
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
       const size_t e = (size_t)e0 + t / tnode;
-      const int q = (int)(t % tnode);
+      const int q = t % tnode;
       const int node = q / r;
       const size_t base = e * s * tnode + q;  // (e, m = 0, q)
+      if (mode == kUpdExtract) {
+        b.uprev[e * tnode + q] = b.U[base + (size_t)(s - 1) * tnode];
+        continue;
+      }
       float x[kMaxS];
-      bool apply_z = false;
-      float* zout = nullptr;
+      float* zout;
       if (mode == kUpdInit) {
         for (int m = 0; m < s; ++m) {
           const float v = (float)b.R[base + (size_t)m * tnode];
           b.V[base + (size_t)m * tnode] = v;
           x[m] = zs * v;
         }
-        apply_z = true;
         zout = b.Z;
-      } else if (mode == kUpdGS || mode == kUpdGSZ) {
+      } else {
         float* w = b.V + (size_t)row * b.L;
         for (int m = 0; m < s; ++m) {
           const size_t o = base + (size_t)m * tnode;
@@ -340,29 +509,13 @@ __global__ void __launch_bounds__(kEngThreads) eng_update_kernel(const __grid_co
           w[o] = acc;
           x[m] = zs * acc;
         }
-        apply_z = mode == kUpdGSZ;
         zout = b.Z + (size_t)row * b.L;
-      } else if (mode == kUpdSolve) {
-        for (int m = 0; m < s; ++m) {
-          const size_t o = base + (size_t)m * tnode;
-          const float acc = rows_sum(cf, b.Z + o, b.L, k);
-          const double u = b.U[o] + (double)acc;
-          b.U[o] = u;
-          b.U32[o] = (float)u;
-        }
-      } else if (mode == kUpdExtract) {
-        b.uprev[e * tnode + q] = b.U[base + (size_t)(s - 1) * tnode];
       }
-      if (apply_z && b.pbtm) {  // temporal-mass scaling: z_m = x_m / omega_m
-        const OpArgs<float>& a = L.a32[item.slot];
-        for (int m = 0; m < s; ++m) zout[base + (size_t)m * tnode] = x[m] * a.inv_omega[m];
-      } else if (apply_z && !b.kron && !b.fdm) {  // Kron / fdm slots: z is formed by their own kernels
-        const float* P = b.Pinv + (e * s * s) * nd + node;
-        for (int m = 0; m < s; ++m) {
-          float z = 0.f;
-          for (int jj = 0; jj < s; ++jj) z = fmaf(P[(size_t)(m * s + jj) * nd], x[jj], z);
-          zout[base + (size_t)m * tnode] = z;
-        }
+      const float* P = b.Pinv + (e * s * s) * nd + node;
+      for (int m = 0; m < s; ++m) {
+        float zv = 0.f;
+        for (int jj = 0; jj < s; ++jj) zv = fmaf(P[(size_t)(m * s + jj) * nd], x[jj], zv);
+        zout[base + (size_t)m * tnode] = zv;
       }
     }
     __syncthreads();
@@ -500,8 +653,7 @@ __global__ void eng_init_kernel(const SlotBuf b) {
 cudaError_t eng_tick_tail(const EngLaunch& L, cudaStream_t st) {
   if (L.n_active <= 0) return cudaSuccess;
   eng_dot_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
-  const int warps_per_block = kEngThreads / 32;
-  eng_control_kernel<<<(L.n_active + warps_per_block - 1) / warps_per_block, kEngThreads, 0, st>>>(L);
+  eng_control_kernel<<<L.n_active, kEngThreads, 0, st>>>(L);
   eng_update_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
   if (L.any_kron) eng_kron_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
   if (L.any_fdm) {

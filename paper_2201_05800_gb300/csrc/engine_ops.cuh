@@ -29,10 +29,14 @@ __global__ void __launch_bounds__(256) eng_op_kernel(const __grid_constant__ Eng
   const int n = *L.n_op_items;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const EngItem item = L.op_items[it];
-    if (L.ctl[item.slot].phase != want || !eng_runs(L, L.buf[item.slot])) continue;
+    const SlotBuf& sb = L.buf[item.slot];
     const OpArgs<T>* ga = eng_args<T>(L, item.slot);
-    // one item list serves both precisions: skip tiles beyond this precision's tile count
-    if ((long long)item.idx * ga->epb >= ga->nelem) continue;
+    // a slot in another phase (or past this precision's tile count: one item list serves both
+    // precisions) has nothing more for this block: step past the slot's tiles at once
+    if (L.ctl[item.slot].phase != want || !eng_runs(L, sb) || (long long)item.idx * ga->epb >= ga->nelem) {
+      it += (sb.op0 + sb.nop - it - 1) / (int)gridDim.x * (int)gridDim.x;
+      continue;
+    }
     const unsigned* src = reinterpret_cast<const unsigned*>(ga);
     unsigned* dst = reinterpret_cast<unsigned*>(&ks);
     for (int i = threadIdx.x; i < (int)(sizeof(OpArgs<T>) / 4); i += blockDim.x) dst[i] = src[i];

@@ -60,7 +60,9 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
-// Bounded wait for phase `parity` of `bar`; false when the limit ran out.
+// Bounded wait for phase `parity` of `bar`; false when the limit ran out.  A failed poll backs
+// off for a few tens of nanoseconds, so that the waiting warp does not take issue slots from the
+// warps of the other CTAs on the SM while the copy is in flight.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit) {
   const unsigned a = smem_u32(bar);
   for (long long i = 0; i < limit; ++i) {
@@ -71,6 +73,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long l
         : "r"(a), "r"(parity)
         : "memory");
     if (ok) return true;
+    __nanosleep(32);
   }
   return false;
 }
