@@ -22,9 +22,10 @@ namespace {
 
 constexpr size_t kAlign = 256;
 // values per work item of the build / dot / update kernels: a power of two in [kChunkMin, kChunkMax]
-// near L / (2 SMs), so that a slot alone spreads over the whole GPU and a large one keeps few
-// partial sums (it depends on the slot and the device only, not on the other slots)
-constexpr size_t kChunkMin = 2048, kChunkMax = 16384;
+// near L / (4 SMs), so that a slot alone fills the four resident blocks per SM of those kernels in
+// about one wave, and a large one keeps few partial sums (it depends on the slot and the device
+// only, not on the other slots)
+constexpr size_t kChunkMin = 2048, kChunkMax = 65536;
 constexpr size_t kOpSmemCap = 96 * 1024;
 constexpr size_t kFdmMaxLine = 4096;  // complex values of one x-line group or one y column of the fdm passes
 
@@ -126,6 +127,7 @@ struct stdg_batch {
   // host lists
   std::vector<int> active;
   int n_op = 0, n_chunk = 0;
+  int max_nitems = 0;  // most chunk items of one active slot (width of the controller blocks)
   bool dirty = true;
   size_t smem64 = 0, smem32 = 0;
   std::string err;
@@ -315,6 +317,7 @@ cudaError_t probe(const stdg_batch* b, int mode, const OpArgs<double>& a64, cons
 stdg_status rebuild(stdg_batch* b) {
   std::vector<EngItem> op, ch, frows, fcols;
   b->smem64 = b->smem32 = 0;
+  b->max_nitems = 0;
   b->any_fdm = false;
   b->fdm_smem[0] = b->fdm_smem[1] = b->fdm_smem[2] = 0;
   b->any_kron = false;
@@ -330,6 +333,7 @@ stdg_status rebuild(stdg_batch* b) {
     for (long long t = 0; t < std::max(tiles, tiles32); ++t) op.push_back({id, (int)t});
     hs.buf.item0 = (int)ch.size();
     for (int c = 0; c < hs.buf.nitems; ++c) ch.push_back({id, c});
+    b->max_nitems = std::max(b->max_nitems, hs.buf.nitems);
     if (hs.buf.fdm) {
       b->any_fdm = true;
       for (int r = 0; r < l.ky * l.s; ++r) frows.push_back({id, r});
@@ -416,6 +420,7 @@ stdg_status tick(stdg_batch* b) {
   L.n_chunk_items = b->counts + 1;
   L.active = b->active_d;
   L.n_active = (int)b->active.size();
+  L.ctl_threads = b->max_nitems > kCtlWideItems ? 32 * kCtlWideWarps : kEngThreads;
   const size_t smem = std::max(b->smem64, b->smem32);
   const int per_sm = std::max(1, std::min(8, (int)(233472 / (smem + 1024))));
   L.op_grid = std::max(1, std::min(b->n_op, b->sms * per_sm));
@@ -874,7 +879,7 @@ stdg_status stdg_batch_add(stdg_batch* b, const stdg_config_desc* d, const doubl
   sb.r = l.r;
   sb.L = l.L;
   size_t chunk = kChunkMin;
-  while (chunk < kChunkMax && chunk < l.L / (2 * (size_t)b->sms)) chunk <<= 1;
+  while (chunk < kChunkMax && chunk < l.L / (4 * (size_t)b->sms)) chunk <<= 1;
   sb.chunk_elems = std::max(1, (int)(chunk / ((size_t)l.s * l.nd * l.r)));
   sb.nitems = (int)((l.nelem + sb.chunk_elems - 1) / sb.chunk_elems);
   sb.item0 = 0;

@@ -36,6 +36,9 @@ namespace stdg {
 constexpr int kEngMaxM = 31;  // Krylov dimension: basis of m + 1 <= 32 rows
 constexpr int kEngRows = 32;
 constexpr int kEngThreads = 256;
+// The controller block of a slot with more than kCtlWideItems chunk items reduces its partial
+// sums with kCtlWideWarps warps (else kEngThreads / 32); the choice depends on the slot alone.
+constexpr int kCtlWideItems = 512, kCtlWideWarps = 32;
 
 enum EngPhase { kPhIdle = 0, kPhResid = 1, kPhArnoldi = 2, kPhReorth = 3, kPhDone = 4 };
 enum EngUpd { kUpdNone = 0, kUpdInit = 1, kUpdGS = 2, kUpdGSZ = 3, kUpdSolve = 4, kUpdExtract = 5 };
@@ -96,6 +99,7 @@ struct EngLaunch {
   const int* n_chunk_items;
   const int* active;  // active slot ids
   int n_active;
+  int ctl_threads;  // block size of the controller: 32 kCtlWideWarps when a slot needs the wide reduction
   int op_grid, chunk_grid;
   size_t op_smem64, op_smem32;
   OpArgs<double>* a64;

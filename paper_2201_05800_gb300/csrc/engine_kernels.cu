@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kEngThreads, 4) eng_dot_kernel(const __grid_co
 
 // Shared-memory copy of what the controller of one slot touches in a tick.
 struct CtlShared {
-  double red[kEngThreads / 32][kEngRows];  // per-warp sums of each row
+  double red[kCtlWideWarps][kEngRows];  // per-warp sums of each row
   double P[kEngRows];                      // the tick's reduced dot products
   double h[kEngRows + 1];                  // column j of H
   double cs[kEngRows], sn[kEngRows], sig[kEngRows + 1];
@@ -184,19 +184,21 @@ __device__ int finish_column(SlotCtl& c, const SlotBuf& b, OpArgs<float>& a32, d
 }
 
 // One block per active slot (grid = number of active slots).  The block reduces the
-// slot's per-item partial sums: warp w takes the groups of kA consecutive items
+// slot's per-item partial sums: warp w < W takes the groups of kA consecutive items
 // w, w + W, w + 2W, ... (kA loads in flight per lane, lane = row), each warp combines its
 // kA running sums in a fixed tree and the warps' sums are added in warp order, so the
-// result does not depend on timing.  Thread 0 then runs the Newton / Arnoldi logic on a
-// shared-memory copy of the Givens data; at the end of a cycle the block stages H's
-// leading block for the triangular solve.
-__global__ void __launch_bounds__(kEngThreads) eng_control_kernel(const __grid_constant__ EngLaunch L) {
-  constexpr int W = kEngThreads / 32, kA = 8;
+// result does not depend on timing; W depends on the slot's item count only (not on the
+// block size, which follows the largest slot of the batch).  Thread 0 then runs the
+// Newton / Arnoldi logic on a shared-memory copy of the Givens data; at the end of a
+// cycle the block stages H's leading block for the triangular solve.
+__global__ void __launch_bounds__(32 * kCtlWideWarps) eng_control_kernel(const __grid_constant__ EngLaunch L) {
+  constexpr int kA = 8;
   __shared__ CtlShared S;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int slot = L.active[blockIdx.x];
   SlotCtl& c = L.ctl[slot];
   const SlotBuf& b = L.buf[slot];
+  const int W = b.nitems > kCtlWideItems ? kCtlWideWarps : kEngThreads / 32;
   const int ph = c.phase;
   if ((ph != kPhResid && ph != kPhArnoldi && ph != kPhReorth) || !eng_runs(L, b)) {
     if (threadIdx.x == 0) c.upd = kUpdNone;
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(kEngThreads) eng_control_kernel(const __grid_c
   }
   const int k = ph == kPhResid ? 1 : c.j + 2;
   const int j = c.j;
-  if (lane < k) {
+  if (lane < k && wid < W) {
     const double* pp = L.partials + (size_t)b.item0 * kEngRows + lane;
     const int nit = b.nitems;
     double acc[kA];
@@ -405,7 +407,8 @@ __device__ __forceinline__ void linear_update(const EngLaunch& L, const SlotBuf&
     if (a0 > v1) a0 = v1;
     a1 = a0 + ((v1 - a0) & ~(size_t)3);
   }
-  // temporal node of value v (v0 starts an element block; a chunk holds at most a few thousand values)
+  // temporal node of value v (v0 starts an element block; a chunk holds at most 65,536 values or
+  // one element block)
   auto tnode_of = [&](size_t v) { return ((int)(v - v0) / tnode) % b.s; };
   for (size_t q = a0 / 4 + threadIdx.x; q < a1 / 4; q += blockDim.x) {
     const size_t v = 4 * q;
@@ -482,7 +485,7 @@ __global__ void __launch_bounds__(kEngThreads) eng_update_kernel(const __grid_co
     }
     const int s = b.s, nd = b.nd, r = b.r;
     const int tnode = nd * r;
-    const int total = (int)(e1 - e0) * tnode;  // a chunk holds at most a few thousand values
+    const int total = (int)(e1 - e0) * tnode;  // a chunk holds at most 65,536 values or one element block
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
       const size_t e = (size_t)e0 + t / tnode;
       const int q = t % tnode;
@@ -653,7 +656,7 @@ __global__ void eng_init_kernel(const SlotBuf b) {
 cudaError_t eng_tick_tail(const EngLaunch& L, cudaStream_t st) {
   if (L.n_active <= 0) return cudaSuccess;
   eng_dot_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
-  eng_control_kernel<<<L.n_active, kEngThreads, 0, st>>>(L);
+  eng_control_kernel<<<L.n_active, L.ctl_threads, 0, st>>>(L);
   eng_update_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
   if (L.any_kron) eng_kron_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
   if (L.any_fdm) {
