@@ -128,6 +128,7 @@ struct stdg_batch {
   std::vector<int> active;
   int n_op = 0, n_chunk = 0;
   int max_nitems = 0;  // most chunk items of one active slot (width of the controller blocks)
+  int op_occ[2] = {1, 1};  // resident blocks per SM of the residual and Jv op kernels (set by rebuild)
   bool dirty = true;
   size_t smem64 = 0, smem32 = 0;
   std::string err;
@@ -392,6 +393,7 @@ stdg_status rebuild(stdg_batch* b) {
     std::memset(&L, 0, sizeof(L));
     L.op_smem64 = b->smem64;
     L.op_smem32 = b->smem32;
+    L.occ = b->op_occ;
     BCK(b, physics(b, L, 1));
     if (b->any_fdm) {
       L.fdm_smem_a = b->fdm_smem[0];
@@ -421,9 +423,9 @@ stdg_status tick(stdg_batch* b) {
   L.active = b->active_d;
   L.n_active = (int)b->active.size();
   L.ctl_threads = b->max_nitems > kCtlWideItems ? 32 * kCtlWideWarps : kEngThreads;
-  const size_t smem = std::max(b->smem64, b->smem32);
-  const int per_sm = std::max(1, std::min(8, (int)(233472 / (smem + 1024))));
-  L.op_grid = std::max(1, std::min(b->n_op, b->sms * per_sm));
+  L.op_grid64 = std::max(1, std::min(b->n_op, b->sms * std::max(1, b->op_occ[0])));
+  L.op_grid32 = std::max(1, std::min(b->n_op, b->sms * std::max(1, b->op_occ[1])));
+  L.occ = nullptr;
   L.chunk_grid = std::max(1, std::min(b->n_chunk, b->sms * 8));
   L.op_smem64 = b->smem64;
   L.op_smem32 = b->smem32;

@@ -100,7 +100,8 @@ struct EngLaunch {
   const int* active;  // active slot ids
   int n_active;
   int ctl_threads;  // block size of the controller: 32 kCtlWideWarps when a slot needs the wide reduction
-  int op_grid, chunk_grid;
+  int op_grid64, op_grid32, chunk_grid;  // residual / Jv grids: the SMs x each kernel's resident blocks
+  int* occ;  // prepare only (host): resident blocks per SM of the residual and Jv kernels, [2]
   size_t op_smem64, op_smem32;
   OpArgs<double>* a64;
   OpArgs<float>* a32;

@@ -39,14 +39,16 @@ __device__ __forceinline__ void block_reduce_store(const double (&accd)[KB], int
   __syncthreads();
 }
 
-// V_i . w over [v0, v1) for i < k, in passes over groups of 8 rows (few registers, so many
-// blocks stay resident; w is re-read from L1/L2 once per group).  When the rows start on
-// 16 bytes the aligned body of the range is read in 16-byte words (four values per load),
-// the at most three values before and after it one by one.  Per-warp sums of each row go to
+// V_i . w over [v0, v1) for i < k, in passes over groups of kDotRows rows (w is re-read from
+// L1/L2 once per group).  The pass is bound by memory latency, so each thread keeps one
+// 16-byte load of every row of the group in flight.  When the rows start on 16 bytes the
+// aligned body of the range is read in 16-byte words (four values per load), the at most
+// three values before and after it one by one.  Per-warp sums of each row go to
 // red[warp][row]; then one fixed-order sum.
+constexpr int kDotRows = 16;
 __device__ __forceinline__ void dot_rows(const SlotBuf& b, size_t v0, size_t v1, int j, int k,
                                          double (*red)[kEngRows], double* out) {
-  constexpr int G = 8;
+  constexpr int G = kDotRows;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const float* w = b.V + (size_t)(j + 1) * b.L;
   size_t a0 = v0, a1 = v0;  // 16-byte body [a0, a1)
@@ -96,7 +98,7 @@ __device__ __forceinline__ void dot_rows(const SlotBuf& b, size_t v0, size_t v1,
 // partials[item][i], i < k: |R|^2 over the chunk (kPhResid) or V_i . w with
 // w = V_{j+1} (kPhArnoldi, kPhReorth; k = j + 2, per-thread sums in FP32 as in
 // the single-slab mixed path, cross-thread sums in FP64 in a fixed order).
-__global__ void __launch_bounds__(kEngThreads, 4) eng_dot_kernel(const __grid_constant__ EngLaunch L) {
+__global__ void __launch_bounds__(kEngThreads, 2) eng_dot_kernel(const __grid_constant__ EngLaunch L) {
   __shared__ double red[kEngThreads / 32][kEngRows];
   const int n = *L.n_chunk_items;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {

@@ -67,8 +67,9 @@ inline cudaError_t eng_smem_attr(K kern, size_t smem) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-// prepare = 1: only set the shared-memory attributes of the op kernels (outside any
-// stream capture); prepare = 0: launch build, residual and Jv kernels of one tick.
+// prepare = 1: only set the shared-memory attributes of the op kernels and report their
+// resident blocks per SM at those sizes in L.occ (outside any stream capture); prepare = 0:
+// launch build, residual and Jv kernels of one tick.
 template <int DIM, int EQ>
 cudaError_t eng_physics_inst(const EngLaunch& L, cudaStream_t st, int prepare) {
   auto k64 = eng_op_kernel<DIM, EQ, double, kModeResidual>;
@@ -76,12 +77,16 @@ cudaError_t eng_physics_inst(const EngLaunch& L, cudaStream_t st, int prepare) {
   if (prepare) {
     cudaError_t e = eng_smem_attr(k64, L.op_smem64);
     if (e != cudaSuccess) return e;
-    return eng_smem_attr(k32, L.op_smem32);
+    e = eng_smem_attr(k32, L.op_smem32);
+    if (e != cudaSuccess || !L.occ) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L.occ[0], k64, 256, L.op_smem64);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L.occ[1], k32, 256, L.op_smem32);
   }
   if (L.n_active <= 0) return cudaSuccess;
   eng_build_kernel<DIM, EQ><<<L.chunk_grid, 128, 0, st>>>(L);
-  k64<<<L.op_grid, 256, L.op_smem64, st>>>(L, kPhResid);
-  k32<<<L.op_grid, 256, L.op_smem32, st>>>(L, kPhArnoldi);
+  k64<<<L.op_grid64, 256, L.op_smem64, st>>>(L, kPhResid);
+  k32<<<L.op_grid32, 256, L.op_smem32, st>>>(L, kPhArnoldi);
   return cudaGetLastError();
 }
 
