@@ -1066,7 +1066,7 @@ def _density_wave_leg(stdg, stream, slabs=2):
 
 
 def _hbm_peak():
-    """(GB/s, source): the measured copy bandwidth of this machine, else the fallback figure."""
+    """(GB/s, source): the measured copy bandwidth in MEASURED_PEAKS.json, else the fallback figure."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(p) as f:

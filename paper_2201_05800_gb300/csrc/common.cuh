@@ -70,6 +70,8 @@ struct OpArgs {
   // temporal nodes split over CTAs: CTA b works on element tile b / msplit and on the
   // temporal nodes m = b % msplit, b % msplit + msplit, ... (0 or 1: one CTA per tile)
   int msplit;
+  // jv_tangent_kernel: tile distance of the L2 prefetch (the CTAs resident at once), 0 = none
+  int prefetch;
   double* v0d;
   float* v0f;
   // error word of kernels with bounded waits (bit 0: a wait gave up), or null

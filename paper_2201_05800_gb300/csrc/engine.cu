@@ -128,6 +128,7 @@ struct stdg_batch {
   std::vector<int> active;
   int n_op = 0, n_chunk = 0;
   int max_nitems = 0;  // most chunk items of one active slot (width of the controller blocks)
+  bool any_wide = false;  // some active slot takes the 16-row dot pass
   int op_occ[2] = {1, 1};  // resident blocks per SM of the residual and Jv op kernels (set by rebuild)
   bool dirty = true;
   size_t smem64 = 0, smem32 = 0;
@@ -323,6 +324,8 @@ stdg_status rebuild(stdg_batch* b) {
   b->fdm_smem[0] = b->fdm_smem[1] = b->fdm_smem[2] = 0;
   b->any_kron = false;
   for (int id : b->active) b->any_kron = b->any_kron || b->slots[id].buf.kron;
+  b->any_wide = false;
+  for (int id : b->active) b->any_wide = b->any_wide || b->slots[id].lay.L >= kDotWideLen;
   for (int id : b->active) {
     HostSlot& hs = b->slots[id];
     const Layout& l = hs.lay;
@@ -436,6 +439,7 @@ stdg_status tick(stdg_batch* b) {
   L.partials = b->partials;
   L.tick = b->tick_d;
   L.any_kron = b->any_kron ? 1 : 0;
+  L.any_wide = b->any_wide ? 1 : 0;
   L.fdm_rows = b->fdm_rows;
   L.n_fdm_rows = b->counts + 2;
   L.fdm_cols = b->fdm_cols;

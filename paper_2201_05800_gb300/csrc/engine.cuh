@@ -39,6 +39,8 @@ constexpr int kEngThreads = 256;
 // The controller block of a slot with more than kCtlWideItems chunk items reduces its partial
 // sums with kCtlWideWarps warps (else kEngThreads / 32); the choice depends on the slot alone.
 constexpr int kCtlWideItems = 512, kCtlWideWarps = 32;
+// Slots of at least kDotWideLen values take the dot pass with 16 rows per group.
+constexpr size_t kDotWideLen = (size_t)1 << 21;
 
 enum EngPhase { kPhIdle = 0, kPhResid = 1, kPhArnoldi = 2, kPhReorth = 3, kPhDone = 4 };
 enum EngUpd { kUpdNone = 0, kUpdInit = 1, kUpdGS = 2, kUpdGSZ = 3, kUpdSolve = 4, kUpdExtract = 5 };
@@ -110,6 +112,7 @@ struct EngLaunch {
   double* partials;  // kEngRows per chunk item
   int* tick;         // tick counter (device), advanced by the last launch of a tick
   int any_kron;      // some slot uses the element tensor-product preconditioner
+  int any_wide;      // some slot has at least kDotWideLen values
   // global fast-diagonalisation preconditioner: work items (slot, ey s + m) of the x passes and
   // (slot, kx n + jx) of the y/temporal pass, and the shared memory of each pass
   const EngItem* fdm_rows;

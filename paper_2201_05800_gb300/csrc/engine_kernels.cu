@@ -39,16 +39,15 @@ __device__ __forceinline__ void block_reduce_store(const double (&accd)[KB], int
   __syncthreads();
 }
 
-// V_i . w over [v0, v1) for i < k, in passes over groups of kDotRows rows (w is re-read from
-// L1/L2 once per group).  The pass is bound by memory latency, so each thread keeps one
-// 16-byte load of every row of the group in flight.  When the rows start on 16 bytes the
-// aligned body of the range is read in 16-byte words (four values per load), the at most
-// three values before and after it one by one.  Per-warp sums of each row go to
-// red[warp][row]; then one fixed-order sum.
-constexpr int kDotRows = 16;
+// V_i . w over [v0, v1) for i < k, in passes over groups of G rows (w is re-read from L1/L2
+// once per group).  The pass is bound by memory latency, so each thread keeps one 16-byte
+// load of every row of the group in flight.  When the rows start on 16 bytes the aligned
+// body of the range is read in 16-byte words (four values per load), the at most three
+// values before and after it one by one.  Per-warp sums of each row go to red[warp][row];
+// then one fixed-order sum.
+template <int G>
 __device__ __forceinline__ void dot_rows(const SlotBuf& b, size_t v0, size_t v1, int j, int k,
                                          double (*red)[kEngRows], double* out) {
-  constexpr int G = kDotRows;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const float* w = b.V + (size_t)(j + 1) * b.L;
   size_t a0 = v0, a1 = v0;  // 16-byte body [a0, a1)
@@ -98,7 +97,13 @@ __device__ __forceinline__ void dot_rows(const SlotBuf& b, size_t v0, size_t v1,
 // partials[item][i], i < k: |R|^2 over the chunk (kPhResid) or V_i . w with
 // w = V_{j+1} (kPhArnoldi, kPhReorth; k = j + 2, per-thread sums in FP32 as in
 // the single-slab mixed path, cross-thread sums in FP64 in a fixed order).
-__global__ void __launch_bounds__(kEngThreads, 2) eng_dot_kernel(const __grid_constant__ EngLaunch L) {
+// WIDE = 0: 8 rows per pass, four resident blocks per SM, for the slots below
+// kDotWideLen values; WIDE = 1: 16 rows per pass (twice the loads in flight per
+// thread, two resident blocks per SM) for the longer slots, whose chunks are long
+// streams.  A slot always takes the same kernel, so its sums do not depend on the
+// other slots.
+template <int WIDE>
+__global__ void __launch_bounds__(kEngThreads, WIDE ? 2 : 4) eng_dot_kernel(const __grid_constant__ EngLaunch L) {
   __shared__ double red[kEngThreads / 32][kEngRows];
   const int n = *L.n_chunk_items;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(kEngThreads, 2) eng_dot_kernel(const __grid_co
     const int ph = L.ctl[item.slot].phase;
     if (ph != kPhResid && ph != kPhArnoldi && ph != kPhReorth) continue;
     const SlotBuf b = L.buf[item.slot];
-    if (!eng_runs(L, b)) continue;
+    if ((b.L >= kDotWideLen) != (WIDE != 0) || !eng_runs(L, b)) continue;
     long long e0, e1;
     chunk_range(b, item.idx, &e0, &e1);
     const size_t blockvals = (size_t)b.s * b.nd * b.r;
@@ -118,7 +123,7 @@ __global__ void __launch_bounds__(kEngThreads, 2) eng_dot_kernel(const __grid_co
       block_reduce_store<1>(a, 1, red, out);
     } else {
       const int j = L.ctl[item.slot].j;
-      dot_rows(b, v0, v1, j, j + 2, red, out);
+      dot_rows<WIDE ? 16 : 8>(b, v0, v1, j, j + 2, red, out);
     }
   }
 }
@@ -657,7 +662,8 @@ __global__ void eng_init_kernel(const SlotBuf b) {
 
 cudaError_t eng_tick_tail(const EngLaunch& L, cudaStream_t st) {
   if (L.n_active <= 0) return cudaSuccess;
-  eng_dot_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
+  eng_dot_kernel<0><<<L.chunk_grid, kEngThreads, 0, st>>>(L);
+  if (L.any_wide) eng_dot_kernel<1><<<L.chunk_grid, kEngThreads, 0, st>>>(L);
   eng_control_kernel<<<L.n_active, L.ctl_threads, 0, st>>>(L);
   eng_update_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);
   if (L.any_kron) eng_kron_kernel<<<L.chunk_grid, kEngThreads, 0, st>>>(L);

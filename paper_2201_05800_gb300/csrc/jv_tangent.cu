@@ -21,7 +21,17 @@ cudaError_t launch_one(const OpArgs<float>& k, cudaStream_t st) {
   }
   const int threads = (E * NS * ND + 31) / 32 * 32;
   const long long blocks = (k.nelem + E - 1) / E;
-  kern<<<(unsigned)blocks, threads, smem, st>>>(k);
+  // CTAs resident at once on the device: the distance, in tiles, of each CTA's L2 prefetch
+  static const int resident = [&] {
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess)
+      return 0;
+    return sms * occ;
+  }();
+  OpArgs<float> a = k;
+  a.prefetch = resident;
+  kern<<<(unsigned)blocks, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

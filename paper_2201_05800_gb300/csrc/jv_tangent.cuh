@@ -60,6 +60,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
+// Hint: bring `bytes` (a multiple of 16, 16-byte aligned) from global memory into L2.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Bounded wait for phase `parity` of `bar`; false when the limit ran out.  A failed poll backs
 // off for a few tens of nanoseconds, so that the waiting warp does not take issue slots from the
 // warps of the other CTAs on the SM while the copy is in flight.
@@ -265,6 +270,13 @@ __global__ void __launch_bounds__((E * NS * ipow_c(NP, DIM) + 31) / 32 * 32)
     mbar_expect_tx(&bar, 2 * bytes);
     bulk_g2s(su, k.U + e0 * TILE, bytes, &bar);
     bulk_g2s(sv, k.v + e0 * TILE, bytes, &bar);
+    // the tile of the CTA that starts about one residency later: its copy then comes from L2
+    const long long pe = e0 + (long long)k.prefetch * E;
+    if (k.prefetch > 0 && pe < k.nelem) {
+      const int pn = (int)((k.nelem - pe) < E ? (k.nelem - pe) : E);
+      bulk_prefetch_l2(k.U + pe * TILE, (unsigned)(pn * TILE * sizeof(float)));
+      bulk_prefetch_l2(k.v + pe * TILE, (unsigned)(pn * TILE * sizeof(float)));
+    }
   }
   for (int i = tid; i < DIM * NP * LP; i += blockDim.x) {
     const int a = i / (NP * LP), r = (i / LP) % NP, j = i % LP;

@@ -261,3 +261,32 @@ def test_stiffest_workload_instances_converge(S):
         sl = B.add(items[ids[0]][0], items[ids[0]][1])
         assert B.run(200000) == 0
         assert np.array_equal(B.get_state(sl), mixed[0])
+
+
+def test_long_slot_takes_the_wide_dot_pass(S):
+    """A slot of at least 2^21 values takes the 16-row dot pass (64 x 64 vortex, N = 5, s = 4:
+    2,359,296 values), a small one the 8-row pass.  The long slot's slab agrees with the
+    single-slab FP64 path's (pinned against the oracle at full size elsewhere) to the workload
+    tolerance, and it is bitwise the same alone and next to the small slot."""
+    prob, u0 = _vortex((64, 64), 5, 4)
+    assert 64 * 64 * 36 * 4 * 4 >= 1 << 21
+    small, us = _vortex((4, 4), 3, 3)
+    with S.Context(prob.config(**WORK)) as c:
+        c.set_state(np.ascontiguousarray(u0).ravel())
+        st = c.advance_slab()
+        assert st["status"] == 0, st
+        U_ref = prob.from_ext(c.get_slab())
+    out = []
+    for with_small in (False, True):
+        with S.Batch(2, S.EULER, 4, 4 << 30) as B:
+            if with_small:
+                s_small = B.add(small.config(**WORK), np.ascontiguousarray(us).ravel())
+            sl = B.add(prob.config(**WORK), np.ascontiguousarray(u0).ravel())
+            assert B.run(20000) == 0
+            done, status, stb = B.query(sl)
+            assert done and status == 0, (status, stb)
+            if with_small:
+                assert B.query(s_small)[1] == 0
+            out.append(B.get_slab(sl).copy())
+    assert np.array_equal(out[0], out[1])
+    assert rel_lgl(prob, prob.from_ext(out[0]), U_ref) <= 1e-8
