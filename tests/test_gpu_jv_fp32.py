@@ -33,9 +33,10 @@ def S():
 
 
 # (dim, cells, N, s): the two bulk-copy shapes with ragged last tiles and one-element
-# periodic directions, and a shape served by the general kernel
+# periodic directions, grids with more tiles than the GPU holds CTAs at once (every CTA's L2
+# prefetch of a later tile lands inside the grid), and a shape served by the general kernel
 CASES = [(2, (7, 3), 4, 4), (2, (4, 4), 4, 4), (2, (1, 5), 4, 4), (3, (3, 2, 2), 3, 3), (3, (2, 1, 3), 3, 3),
-         (2, (3, 3), 3, 3), (3, (2, 2, 2), 2, 2)]
+         (3, (13, 12, 12), 3, 3), (2, (55, 50), 4, 4), (2, (3, 3), 3, 3), (3, (2, 2, 2), 2, 2)]
 
 
 @pytest.mark.parametrize("dim,cells,N,s", CASES)
