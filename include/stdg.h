@@ -196,8 +196,11 @@ stdg_status stdg_spatial_operator(stdg_ctx* ctx, const double* U, double* F, int
  * ((D_tau^T M_tau - e_s e_s^T) (x) I) v + dt/2 (M_tau (x) I) F'(U) v.  Device
  * pointers to slab_len floats each (slab layout; U, v 16-byte aligned for the
  * bulk-copy kernel of the 2D n = 5, s = 4 and 3D n = 4, s = 3 Euler shapes,
- * else the general kernel runs).  Synchronises the context stream; returns
- * STDG_ERR_TIMEOUT if a kernel's bounded wait for its staged tile ran out. */
+ * else the general kernel runs; a context created with STDG_MIXED_BF16 runs
+ * the volume contractions of the 3D shape on the tensor cores, BF16 inputs and
+ * FP32 accumulation).  Synchronises the context stream; returns
+ * STDG_ERR_TIMEOUT if a kernel's bounded wait (staged tile or tensor-core
+ * accumulators) ran out. */
 stdg_status stdg_jv_fp32(stdg_ctx* ctx, const float* U, const float* v, float* Jv);
 
 /* One finite-difference Jacobian-vector launch exactly as GMRES issues it
