@@ -897,6 +897,7 @@ def _batched_leg(stdg, stream, n_inst, n_seq, graphs=1):
 
 
 SERVE_DOF_CAP = 16e6  # smallest-first run: space-time DOF the admitted requests may hold at once
+SERVE_FIFO_CAP = 32e6  # capped arrival-order runs: the same limit for admission in arrival order
 
 
 def _serving_leg(stdg, rates, n_req):
@@ -925,10 +926,12 @@ def _serving_leg(stdg, rates, n_req):
             svc.append(time.perf_counter() - t0)
             seq_status.append(st["status"])
             seq_u.append(c.get_state())
-    # every rate with arrival-order admission, and one rate with smallest-first admission under a
-    # cap on the admitted space-time DOF (stdg_server_set_policy)
+    # every rate with arrival-order admission; one rate with smallest-first admission under a cap on
+    # the admitted space-time DOF, and two with arrival-order admission under a cap
+    # (stdg_server_set_policy)
     pol_rate = rates[min(2, len(rates) - 1)]
     runs = [(str(r), r, 0, 0.0) for r in rates] + [("%d_smallest_first" % pol_rate, pol_rate, 1, SERVE_DOF_CAP)]
+    runs += [("%d_arrival_order_capped" % r, r, 0, SERVE_FIFO_CAP) for r in rates if r in (pol_rate, 1000)]
     first_res = None
     pct = lambda v, q: 1e3 * v[min(len(v) - 1, int(q * len(v)))] if v else None
     for key, rate, order, cap in runs:
@@ -966,7 +969,9 @@ def _serving_leg(stdg, rates, n_req):
     out["scheduling"] = {"graphs": True, "autotune": False,
                          "admission": "arrival order by device memory, except the '<rate>_smallest_first' run: "
                                       "the queued request with the fewest space-time DOF first, while the admitted "
-                                      "ones hold at most %g DOF" % SERVE_DOF_CAP}
+                                      "ones hold at most %g DOF; and the '<rate>_arrival_order_capped' runs: arrival "
+                                      "order while the admitted ones hold at most %g DOF" % (SERVE_DOF_CAP,
+                                                                                            SERVE_FIFO_CAP)}
     out["sequential_path"] = ("stdg_advance_slab per request (FP32 exact Jv, temporal-mass scaling, restarted "
                               "GMRES); service times measured on the GPU, latencies modelled from them under the "
                               "same arrivals with one FIFO queue")
